@@ -1,0 +1,415 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix
+(no GPU).  Each test names the passage or identity it relies on; together
+they are chosen so that a dropped term, a wrong sign or index, or a
+transposed operand anywhere in ``oracle`` fails at least one of them."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import synth
+from oracle import fstat as F
+from oracle import geometry as G
+from oracle import inject as I
+from oracle import resample as R
+from oracle import timemap as TM
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_facts.json")
+NOGAPS = np.zeros((0, 2), np.int64)
+
+
+def facts():
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+def small_plan(**kw):
+    base = dict(dt=0.5, n_data=2048, n_fft=4096, f_het=100.0)
+    base.update(kw)
+    return synth.PlanDesc(**base)
+
+
+# ---------------------------------------------------------------- geometry
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_beam_closed_form_is_tensor_form_up_to_orthogonal_map(seed):
+    """Eqs. 2-3: a, b from the JKS closed form and from d:eps_+, d:eps_x must
+    be related by one constant orthogonal 2x2 map (a change of polarisation
+    basis).  A wrong coefficient makes the map time-dependent or
+    non-orthogonal."""
+    g = synth.rng(seed)
+    det = synth.Detector(lat_rad=g.uniform(-1.4, 1.4), lon_rad=g.uniform(-3, 3),
+                         gamma_rad=g.uniform(0, math.pi))
+    plan = synth.PlanDesc(det=det)
+    alpha, delta = g.uniform(0, 2 * math.pi), math.asin(g.uniform(-1, 1))
+    t = np.linspace(0, 3 * 86400, 3001)
+    a, b = G.beam_ab(t, alpha, delta, plan.det, plan.eph)
+    fp, fx = G.antenna_tensor(t, alpha, delta, 0.0, plan.det, plan.eph)
+    X = np.stack([a, b], 1)
+    Y = np.stack([fp, fx], 1)
+    M, *_ = np.linalg.lstsq(X, Y, rcond=None)
+    assert np.max(np.abs(X @ M - Y)) < 1e-12
+    assert np.allclose(M.T @ M, np.eye(2), atol=1e-12)
+
+
+def test_beam_zenith_unit_response():
+    """Sec. II after Eq. 3 (zeta = 90 deg): for a source at the zenith the
+    response to an optimally oriented wave is 1, i.e. a^2 + b^2 = 1."""
+    assert facts()["arm_angle_deg"]["zeta"] == 90.0
+    plan = synth.PlanDesc()
+    t = 12345.0
+    theta = float(G.sidereal_angle(t, plan.eph, plan.det))
+    a, b = G.beam_ab(t, theta, plan.det.lat_rad, plan.det, plan.eph)
+    assert abs(a * a + b * b - 1.0) < 1e-13
+
+
+def test_roemer_delay_magnitudes_and_rate():
+    """Eq. 4pt2 and Eq. 11c with the analytic ephemeris: |t_m| <= (AU + R)/c,
+    the orbital amplitude is AU/c = 499.005 s for a source in the ecliptic,
+    the Doppler factor is of order 1e-4 (text after Eq. 11c) and is the time
+    derivative of t_m."""
+    plan = synth.PlanDesc()
+    f = facts()["max_doppler"]
+    t = np.linspace(0, plan.eph.year_s, 20001)
+    # ecliptic pole direction has no orbital term; ecliptic source has it all
+    eps = plan.eph.obliquity_rad
+    a_ecl, d_ecl = 0.0, 0.0     # vernal equinox lies in the ecliptic
+    tm = G.roemer_delay(t, a_ecl, d_ecl, plan.det, plan.eph)
+    au_c = plan.eph.au_m / G.C_LIGHT
+    r_c = plan.det.radius_m / G.C_LIGHT
+    assert abs(au_c - 499.00478) < 1e-4
+    assert np.max(np.abs(tm)) <= au_c + r_c + 1e-9
+    assert np.max(tm) > au_c - r_c - 1e-3
+    rate = G.roemer_rate(t, a_ecl, d_ecl, plan.det, plan.eph)
+    assert 0.5 * f["order"] < np.max(np.abs(rate)) < 2 * f["order"]
+    h = 1.0
+    fd = (G.roemer_delay(t + h, a_ecl, d_ecl, plan.det, plan.eph)
+          - G.roemer_delay(t - h, a_ecl, d_ecl, plan.det, plan.eph)) / (2 * h)
+    assert np.max(np.abs(fd - rate)) < 1e-12
+    # ecliptic pole: only the diurnal term of amplitude R cos(lat)/c survives
+    ap, dp = -math.pi / 2, math.pi / 2 - eps
+    tmp = G.roemer_delay(t[:2000], ap, dp, plan.det, plan.eph)
+    assert np.max(np.abs(tmp)) < r_c + 1e-9
+
+
+def test_inverse_map_residual():
+    """Eq. 21 inverted by fixed-point iteration: T^k + t_m(T^k) = t_b^k."""
+    plan = synth.search_plan()
+    tm = synth.make_templates(1.3, -0.4, 0.0, 0, plan.n_data)[0]
+    tb, T, n_b = TM.resample_times(tm, plan)
+    res = T + G.roemer_delay(T, 1.3, -0.4, plan.det, plan.eph) - tb
+    assert np.max(np.abs(res)) < 1e-9
+    # grid: t_b^k uniform, and the last point within dt of t_b(t_e)
+    t_s, t_e = TM.span_times(tm, plan)
+    tbe = t_e + float(G.roemer_delay(t_e, 1.3, -0.4, plan.det, plan.eph))
+    assert tb[-1] <= tbe + 1e-9 and tb[-1] > tbe - plan.dt
+    assert abs(n_b - plan.n_data) < 2 * 1e-4 * plan.n_data
+
+
+# ---------------------------------------------------------------- heterodyne / injection model
+
+def test_heterodyne_worked_example():
+    """Sec. III.A.1 worked example: heterodyning at 995 Hz moves 990 Hz to
+    -5 Hz and 1000 Hz to +5 Hz; keeping every 100th point of the 1 kHz-rate
+    stream gives 10 Hz sampling.  The oracle's reading x_h = x e^{-2 pi i f_h t}
+    must reproduce it."""
+    ex = facts()["heterodyne_example"]
+    fs = 1000.0 * 8                      # well above 2 kHz
+    t = np.arange(int(fs * 20)) / fs
+    for f_in, f_out in [(ex["band_hz"][1], ex["high_edge_after_hz"]),
+                        (ex["band_hz"][0], ex["low_edge_after_hz"])]:
+        x = np.exp(2j * np.pi * f_in * t)          # analytic tone
+        xh = x * np.exp(-2j * np.pi * ex["f_het_hz"] * t)
+        spec = np.fft.fftshift(np.fft.fft(xh))
+        fr = np.fft.fftshift(np.fft.fftfreq(t.size, 1 / fs))
+        assert abs(fr[np.argmax(np.abs(spec))] - f_out) < 1e-9
+    assert fs / 8 / ex["decimation"] == ex["sample_rate_after_hz"]
+
+
+def test_injection_is_positive_frequency_half_of_real_strain():
+    """Eq. 1 with h_+ = A_+ cos Psi, h_x = A_x sin Psi: demodulating the real
+    strain by its own phase over many cycles leaves the complex amplitude
+    (F_+ A_+ - i F_x A_x)/2 that ``inject.signal`` uses."""
+    plan = synth.PlanDesc(f_het=995.0, dt=0.5)
+    inj = synth.random_injection(7, df=0.7, fdot=0.0)
+    h0 = 1.0
+    fs = 16000.0
+    t0 = 4321.0
+    t = t0 + np.arange(int(fs * 2.0)) / fs
+    tm = G.roemer_delay(t, inj.alpha, inj.delta, plan.det, plan.eph)
+    tau = t - plan.t_start + tm
+    psi = inj.phi0 + 2 * np.pi * (plan.f_het + inj.df) * tau
+    Fp, Fx = G.antenna_tensor(t, inj.alpha, inj.delta, inj.psi, plan.det, plan.eph)
+    Ap, Ax = h0 * (1 + inj.cosi ** 2) / 2, h0 * inj.cosi
+    h = Fp * Ap * np.cos(psi) + Fx * Ax * np.sin(psi)
+    amp = np.mean(h * np.exp(-1j * psi))
+    # inject.signal at the window's midpoint, divided by its own phase factor
+    tt = t0 + 1.0
+    p1 = synth.PlanDesc(f_het=995.0, dt=1.0 / fs, t_start=tt, n_data=1,
+                        det=plan.det, eph=plan.eph)
+    s = I.signal(inj, p1, n_data=1, h0=h0)[0]
+    tmm = float(G.roemer_delay(tt, inj.alpha, inj.delta, plan.det, plan.eph))
+    # with t_start = tt: tau = t_m, and x_h's phase is Phi_0 + 2 pi (f_h + df) t_m
+    amp_inj = s / np.exp(1j * (inj.phi0 + 2 * np.pi * (p1.f_het + inj.df) * tmm))
+    assert abs(amp - amp_inj) < 2e-4 * max(abs(amp), 1e-3)
+
+
+# ---------------------------------------------------------------- resampling pieces
+
+def test_sinc_interpolator_tap_positions():
+    """Truncated windowed sinc on a slowly varying tone reproduces the tone
+    (a tap shifted by one sample would be off by ~30 %)."""
+    n = 400
+    j = np.arange(n)
+    nu = 0.03
+    x = np.exp(2j * np.pi * nu * j)
+    u = np.linspace(10.0, 380.0, 1777)
+    valid = np.ones(n, bool)
+    # Lanczos is accurate to ~3e-3 here; plain truncation has the ~6 %
+    # ripple of a truncated Dirichlet kernel; a one-sample shift errs by ~0.19
+    for window, tol in ((R.WIN_LANCZOS, 5e-3), (R.WIN_RECT, 8e-2)):
+        z = R.interpolate(x, u, valid, R.SINC, 8, window)
+        assert np.max(np.abs(z - np.exp(2j * np.pi * nu * u))) < tol
+    # at integer positions the interpolator returns the sample itself
+    z = R.interpolate(x, np.arange(20.0, 30.0), valid, R.SINC, 8, R.WIN_LANCZOS)
+    assert np.allclose(z, x[20:30], atol=1e-15)
+    zn = R.interpolate(x, np.array([20.49, 20.51]), valid, R.NEAREST)
+    assert zn[0] == x[20] and zn[1] == x[21]
+
+
+def test_gap_taps_and_mask():
+    """Sec. III.B, gaps: samples in a gap contribute nothing; the mask
+    follows the nearest-neighbour source."""
+    n = 100
+    x = np.ones(n, np.complex128)
+    valid = R.valid_samples(n, 5, 90, np.array([[40, 50]]))
+    assert valid[5] and not valid[4] and not valid[40] and valid[50] and not valid[95]
+    u = np.array([39.4, 39.6, 49.4, 49.6, 4.4, 4.6])
+    m = R.mask(u, valid)
+    assert list(m) == [1, 0, 0, 1, 0, 1]
+    z = R.interpolate(x, np.array([45.0]), valid, R.SINC, 8, R.WIN_LANCZOS)
+    assert abs(z[0]) < 1e-15
+
+
+# ---------------------------------------------------------------- F-statistic
+
+def _brute_force_two_f(r, plan, n_fft):
+    k = np.arange(r["n_b"])
+    q = np.arange(n_fft)
+    df = (q - n_fft // 2) / (n_fft * plan.dt)
+    E = np.exp(-2j * np.pi * np.outer(df, k * plan.dt))
+    Fa = E @ r["wa"]
+    Fb = E @ r["wb"]
+    return F.two_f(Fa, Fb, r["A"], r["B"], r["C"], plan.sigma2)
+
+
+@pytest.mark.parametrize("interp", [R.NEAREST, R.SINC])
+def test_fft_matches_brute_force_dft(interp):
+    """Step 6 (Eqs. 19-20): the FFT of the zero-padded weighted series with
+    the ascending-frequency reordering equals an O(N^2) DFT evaluated at
+    df_q = (q - N/2)/(N dt)."""
+    plan = synth.PlanDesc(dt=0.5, n_data=200, n_fft=256, interp=interp, f_het=37.0)
+    x = synth.complex_noise(plan.n_data, 1.0, 11)
+    tm = synth.make_templates(2.0, 0.3, -1e-7, 3, 190)[0]
+    r = F.resample_two_f(x, tm, NOGAPS, plan, return_parts=True)
+    bf = _brute_force_two_f(r, plan, plan.n_fft)
+    assert np.max(np.abs(r["two_f"] - bf)) < 1e-9 * max(1.0, np.max(bf))
+
+
+@pytest.mark.parametrize("interp", [R.NEAREST, R.SINC])
+def test_zero_ephemeris_resampling_equals_direct(interp):
+    """With AU = R = 0 the Roemer delay vanishes, T^k = t_b^k falls on the
+    data grid, interpolation is exact, and the resampling 2F must equal direct
+    demodulation (Eqs. 7-8) at every FFT bin, gaps included."""
+    eph = synth.Ephem(au_m=0.0)
+    det = synth.Detector(radius_m=0.0)
+    plan = synth.PlanDesc(dt=0.5, n_data=3000, n_fft=4096, interp=interp,
+                          f_het=50.0, det=det, eph=eph)
+    x = synth.complex_noise(plan.n_data, 1.0, 5)
+    gaps = np.array([[400, 650], [1700, 1800]], np.int64)
+    x = synth.zero_gaps(x, gaps)
+    tm = synth.make_templates(0.7, 0.2, -3e-8, 10, 2900, 0, 2)[0]
+    r = F.resample_two_f(x, tm, gaps, plan, return_parts=True)
+    assert r["n_b"] == 2900
+    fr = F.bin_frequencies(plan.n_fft, plan.dt)
+    sel = np.arange(0, plan.n_fft, 37)
+    d = F.direct_two_f(x, tm, gaps, plan, fr[sel])
+    assert np.max(np.abs(r["two_f"][sel] - d)) < 1e-9 * np.max(d)
+
+
+@pytest.mark.parametrize("seed,fdot,f_het", [(1, 0.0, 100.0), (2, -1e-8, 1000.0),
+                                              (3, -3e-9, 400.0)])
+def test_noise_free_direct_demod_gives_rho2(seed, fdot, f_het):
+    """Eq. 6 with Eqs. 7-10: for noise-free data at the true template the
+    maximised statistic recovers all signal power, 2F = rho^2 (the
+    non-centrality of Sec. IV.B), gaps included."""
+    plan = synth.PlanDesc(dt=0.5, n_data=40000, f_het=f_het)
+    gaps = np.array([[5000, 9000], [20000, 21000]], np.int64)
+    valid = I.valid_all(plan, gaps)
+    inj = synth.random_injection(seed, df=0.31, fdot=fdot)
+    x, info = I.inject(np.zeros(plan.n_data), [inj], plan, valid)
+    tm = synth.make_templates(inj.alpha, inj.delta, fdot, 0, plan.n_data, 0, 2)[0]
+    d = F.direct_two_f(x, tm, gaps, plan, [inj.df])[0]
+    assert abs(d - info[0][1]) < 1e-9 * info[0][1]
+    assert abs(info[0][1] - 400.0) < 1e-9
+
+
+def test_spindown_and_heterodyne_signs():
+    """Eq. 7 with Eq. 5 (demodulate by exp(-i Phi_s)) and the 995 Hz example
+    (x_h = x exp(-2 pi i f_h t)): the true signs recover rho^2; flipping the
+    spindown loses most of it, and the resampled peak lands at +df."""
+    plan = synth.PlanDesc(dt=0.5, n_data=86400, n_fft=1 << 17, f_het=200.0,
+                          interp=R.SINC)
+    valid = I.valid_all(plan)
+    df = 2000 / (plan.n_fft * plan.dt)          # on-grid, +0.0305 Hz
+    inj = synth.random_injection(4, df=df, fdot=-2e-8)
+    x, info = I.inject(np.zeros(plan.n_data), [inj], plan, valid)
+    good = synth.make_templates(inj.alpha, inj.delta, inj.fdot, 0, plan.n_data)[0]
+    bad = synth.make_templates(inj.alpha, inj.delta, -inj.fdot, 0, plan.n_data)[0]
+    r = F.resample_two_f(x, good, NOGAPS, plan)
+    rb = F.resample_two_f(x, bad, NOGAPS, plan)
+    q = int(np.argmax(r))
+    assert q == plan.n_fft // 2 + 2000
+    assert r[q] > 0.98 * info[0][1]
+    assert np.max(rb) < 0.2 * info[0][1]
+
+
+def test_nearest_neighbour_loss_is_sinc_squared():
+    """Sec. V.B: interpolation loses power towards the band edge (of order
+    30 %).  For nearest-neighbour resampling with rounding errors spread
+    uniformly over a sample the expected power factor at df is
+    sinc^2(df dt); at df = 0.7 Hz, dt = 0.5 s this is 0.657."""
+    fct = facts()["interpolation_loss"]
+    plan = synth.PlanDesc(dt=0.5, n_data=10 * 86400 * 2 // 4, n_fft=1 << 19,
+                          interp=R.NEAREST, f_het=100.0)
+    valid = I.valid_all(plan)
+    k = round(0.7 * plan.n_fft * plan.dt)
+    df = k / (plan.n_fft * plan.dt)
+    ratios = []
+    for seed in (21, 22, 23):
+        inj = synth.random_injection(seed, df=df)
+        x, info = I.inject(np.zeros(plan.n_data), [inj], plan, valid)
+        tm = synth.make_templates(inj.alpha, inj.delta, 0.0, 0, plan.n_data)[0]
+        r = F.resample_two_f(x, tm, NOGAPS, plan)
+        ratios.append(r[plan.n_fft // 2 + k] / info[0][1])
+    expect = np.sinc(df * plan.dt) ** 2
+    assert abs(np.mean(ratios) - expect) < 0.05
+    assert abs((1 - expect) - fct["order"]) < 0.1
+
+
+def test_chi2_four_dof_in_noise():
+    """Sec. IV.B: in Gaussian noise 2F is chi^2 with 4 degrees of freedom
+    (mean 4, variance 8), here through the whole resampling path."""
+    dof = facts()["chi2_dof"]["dof"]
+    plan = small_plan(n_data=1024, n_fft=2048, interp=R.NEAREST)
+    tm = synth.make_templates(1.1, 0.5, 0.0, 0, plan.n_data)[0]
+    vals = []
+    for s in range(600):
+        x = synth.complex_noise(plan.n_data, plan.sigma2, 1000 + s)
+        r = F.resample_two_f(x, tm, NOGAPS, plan)
+        vals.extend(r[[100, 700, 1300, 1900]])
+    vals = np.asarray(vals)
+    assert abs(vals.mean() - dof) < 0.15
+    assert abs(vals.var() - 2 * dof) < 1.2
+    assert stats.kstest(vals, "chi2", args=(dof,)).pvalue > 1e-3
+
+
+def test_sinc_noise_mean_matches_tap_energy():
+    """Parseval: for sinc resampling the mean of 2F over all bins in noise is
+    4 times the mean tap energy sum_j w_j^2."""
+    plan = small_plan(n_data=8192, n_fft=16384, interp=R.SINC, window=R.WIN_LANCZOS)
+    tm = synth.make_templates(1.1, 0.5, 0.0, 0, plan.n_data)[0]
+    m = []
+    for s in range(4):
+        x = synth.complex_noise(plan.n_data, plan.sigma2, 50 + s)
+        m.append(np.mean(F.resample_two_f(x, tm, NOGAPS, plan)))
+    assert abs(np.mean(m) / F.noise_gain(plan) - 1.0) < 0.03
+
+
+def test_single_bin_form_matches_fft_bin():
+    """The single-bin DFT used for the gradient equals the FFT path at an
+    FFT bin frequency (the grid-start phase is common to F_a and F_b)."""
+    plan = small_plan(n_data=3000, n_fft=4096, interp=R.SINC)
+    x = synth.complex_noise(plan.n_data, 1.0, 9)
+    tm = synth.make_templates(0.4, -0.9, -2e-9, 0, plan.n_data)[0]
+    r = F.resample_two_f(x, tm, NOGAPS, plan)
+    fr = F.bin_frequencies(plan.n_fft, plan.dt)
+    for q in (0, 17, 2048, 3001):
+        assert abs(F.single_bin_two_f(x, tm, NOGAPS, plan, fr[q]) - r[q]) < 1e-9 * max(r[q], 1)
+
+
+def test_gradient_analytic_in_f_and_fdot():
+    """d2F/df and d2F/dfdot have closed forms from dF_a/df = sum w_a
+    (-2 pi i tau) e and dw/dfdot = -i pi tau^2 w; the finite-difference
+    gradient must agree."""
+    plan = small_plan(n_data=6000, n_fft=8192, interp=R.SINC)
+    x = synth.complex_noise(plan.n_data, 1.0, 77)
+    tm = synth.make_templates(2.2, 0.1, -1e-8, 0, plan.n_data)[0]
+    df = 0.123
+    r = F.resampled_series(x, tm, NOGAPS, plan)
+    tb = r["tb"] - plan.t_start
+    e = np.exp(-2j * np.pi * df * tb)
+    Fa, Fb = np.sum(r["wa"] * e), np.sum(r["wb"] * e)
+    A, B, C = r["A"], r["B"], r["C"]
+    D = A * B - C * C
+
+    def d2f(dFa, dFb):
+        return 2 * (2 * B * np.real(np.conj(Fa) * dFa) + 2 * A * np.real(np.conj(Fb) * dFb)
+                    - 2 * C * np.real(dFa * np.conj(Fb) + Fa * np.conj(dFb))) / (plan.sigma2 * D)
+
+    g_f = d2f(np.sum(r["wa"] * e * (-2j * np.pi * tb)), np.sum(r["wb"] * e * (-2j * np.pi * tb)))
+    g_fd = d2f(np.sum(r["wa"] * e * (-1j * np.pi * tb * tb)),
+               np.sum(r["wb"] * e * (-1j * np.pi * tb * tb)))
+    g = F.single_bin_gradient(x, tm, NOGAPS, plan, df)
+    assert abs(g[2] - g_f) < 1e-6 * abs(g_f)
+    assert abs(g[3] - g_fd) < 1e-5 * abs(g_fd)
+
+
+def test_gradient_vanishes_at_noise_free_truth():
+    """At the true parameters of a noise-free signal 2F is maximal (2F <= rho^2
+    by Cauchy-Schwarz, Eq. 6), so the gradient of the direct statistic is
+    zero; the resampled single-bin statistic inherits it up to the small
+    interpolation error at low df."""
+    plan = synth.PlanDesc(dt=0.5, n_data=40000, n_fft=1 << 16, interp=R.SINC, f_het=100.0)
+    valid = I.valid_all(plan)
+    inj = synth.random_injection(12, df=0.02, fdot=-1e-9)
+    x, info = I.inject(np.zeros(plan.n_data), [inj], plan, valid)
+    tm = synth.make_templates(inj.alpha, inj.delta, inj.fdot, 0, plan.n_data)[0]
+    T = plan.n_data * plan.dt
+    g = F.single_bin_gradient(x, tm, NOGAPS, plan, inj.df)
+    # first-order change over one metric scale must be tiny against rho^2
+    scale = np.array([1e-3, 1e-3, 1.0 / T, 1.0 / T ** 2])
+    assert np.all(np.abs(g * scale) < 2e-3 * info[0][1])
+    # away from the truth the gradient points uphill
+    tm2 = tm.copy()
+    tm2["alpha"] += 2e-3
+    g2 = F.single_bin_gradient(x, tm2, NOGAPS, plan, inj.df + 0.3 / T)
+    f0 = F.single_bin_two_f(x, tm2, NOGAPS, plan, inj.df + 0.3 / T)
+    step = 1e-3 * scale ** 2 * g2 / np.max(np.abs(g2 * scale))
+    tm3 = tm2.copy()
+    tm3["alpha"] += step[0]
+    tm3["delta"] += step[1]
+    tm3["fdot"] += step[3]
+    f1 = F.single_bin_two_f(x, tm3, NOGAPS, plan, inj.df + 0.3 / T + step[2])
+    assert f1 > f0
+
+
+# ---------------------------------------------------------------- inputs
+
+def test_gap_generator():
+    gaps = synth.gap_intervals(100000, 0.1, 2000, 12000, seed=3)
+    assert gaps.shape[1] == 2
+    assert np.all(gaps[:, 1] > gaps[:, 0])
+    assert np.all(gaps[1:, 0] > gaps[:-1, 1])
+    cov = int(np.sum(gaps[:, 1] - gaps[:, 0]))
+    assert 10000 <= cov < 10000 + 12000
+    assert gaps[0, 0] >= 1 and gaps[-1, 1] <= 99999
+
+
+def test_fibonacci_sky_uniform():
+    a, d = synth.fibonacci_sky(4096)
+    assert abs(np.mean(np.sin(d))) < 1e-3
+    assert np.all((a >= 0) & (a < 2 * math.pi))
