@@ -1,0 +1,219 @@
+/*
+ * fstat.h — C ABI of the GB300 barycentric-resampling F-statistic library.
+ *
+ * The library computes, for a batch of templates (sky position alpha, delta
+ * and spindown fdot), the F-statistic 2F in every frequency bin of an
+ * n_fft-point FFT by the barycentric resampling method of Patel, Siemens,
+ * Dupuis & Betzwieser ("Implementation of barycentric resampling for
+ * continuous wave searches in gravitational wave data", LIGO-P0900301),
+ * Sec. III.A.2, whose seven steps are:
+ *
+ *   1. heterodyned, band-limited series x_h(t^k) on a regular detector grid;
+ *   2. heterodyne correction by exp(-2 pi i f_h t_m)            (Eq. absorb);
+ *   3. detector times T^k of a uniform barycentric grid t_b^k  (Eqs. 11, 21);
+ *   4. interpolation z(T^k(t_b^k));
+ *   5. antenna patterns a, b at T^k                              (Eqs. 2-3);
+ *   6. FFTs of a z e^{-i Phi_s} and b z e^{-i Phi_s}  -> F_a, F_b (Eqs. 19-20);
+ *   7. 2F from F_a, F_b and the sums A, B, C, D                  (Eqs. 6, 9).
+ *
+ * Conventions (the paper leaves these open; the library fixes them):
+ *  - times are seconds on the clock of the analytic ephemeris; angles radians;
+ *  - x_h = x exp(-2 pi i f_h (t - t_start)); the output bin q of a template
+ *    holds the frequency offset df = (q - n_fft/2)/(n_fft dt) from f_het, in
+ *    ascending order;
+ *  - Phi_s(tau) = 2 pi fdot tau^2 / 2 with tau = t_b - t_start, removed by
+ *    multiplying with exp(-i Phi_s);
+ *  - 2F = 2 (B|F_a|^2 + A|F_b|^2 - 2 C Re(F_a F_b*)) / (sigma2 D) with the
+ *    masked sums A = sum m a^2, B = sum m b^2, C = sum m a b, D = A B - C^2
+ *    and sigma2 = E|n|^2 of one complex noise sample; 2F is chi^2 with four
+ *    degrees of freedom in Gaussian noise (Sec. IV.B).
+ *
+ * Memory: every data pointer passed to a compute call is a caller-owned
+ * DEVICE buffer (for example a torch tensor) unless stated otherwise.  The
+ * plan owns its descriptor, twiddle tables and a 16-byte status word; scratch
+ * memory (the "workspace") is caller-provided.  Compute calls are
+ * asynchronous on the caller's stream (a cudaStream_t passed as void*, NULL
+ * for the legacy default stream).
+ *
+ * Errors: functions return FSTAT_OK (0) or a negative code.  Argument errors
+ * detected on the host are returned synchronously and nothing is enqueued.
+ * Errors that depend on device data (a template whose span lies outside the
+ * data, an unsorted gap list, n_fft smaller than the resampled length) are
+ * recorded in the plan's device status word, the affected template's output
+ * is filled with NaN, and fstat_status() reports the first such error.
+ */
+#ifndef FSTAT_H
+#define FSTAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ codes */
+#define FSTAT_OK         0
+#define FSTAT_EINVAL    -1  /* null/misaligned pointer, bad size or enum   */
+#define FSTAT_ERANGE    -2  /* value outside the supported range           */
+#define FSTAT_ENOMEM    -3  /* plan allocation failed / workspace too small */
+#define FSTAT_ECUDA     -4  /* a CUDA runtime call failed                  */
+#define FSTAT_ETIMEOUT  -5  /* a bounded device wait ran out               */
+#define FSTAT_ENOTSUP   -6  /* option combination not supported            */
+#define FSTAT_ENOWS     -7  /* no workspace set on the plan                */
+
+/* interpolation (step 4), window of the truncated sinc, precision mode */
+enum { FSTAT_NEAREST = 0, FSTAT_SINC = 1 };
+enum { FSTAT_WIN_RECT = 0, FSTAT_WIN_LANCZOS = 1 };
+enum {
+  FSTAT_PREC_MIXED = 0, /* FP64 time map and phase at knots, FP32 per sample */
+  FSTAT_PREC_FP64  = 1, /* FP64 everywhere (time map, interpolation, FFT)   */
+  FSTAT_PREC_FP32  = 2  /* FP32 everywhere, for the precision study         */
+};
+/* execution mode (fstat_tuning.mode) */
+enum {
+  FSTAT_MODE_FUSED      = 0, /* resample+weight fused into the first FFT pass, batched grids */
+  FSTAT_MODE_PLAIN      = 1, /* one template per launch, unfused stages through HBM          */
+  FSTAT_MODE_PERSISTENT = 2  /* one persistent launch over all (template, tile) work items  */
+};
+
+/* Detector site (Eqs. 2-3 and Eq. 4pt2): geodetic latitude, east longitude,
+ * arm-bisector azimuth gamma counter-clockwise from local East, radius of a
+ * spherical Earth in metres.  Arms at 90 degrees (zeta = 90 deg). */
+typedef struct fstat_detector {
+  double lat_rad, lon_rad, gamma_rad, radius_m;
+} fstat_detector;
+
+/* Analytic ephemeris (Eq. 4pt2): circular orbit of radius au_m in the
+ * ecliptic with period year_s, Sun at the barycentre, sidereal spin period
+ * sidereal_day_s, obliquity, orbital longitude and Greenwich sidereal angle
+ * at t = 0. */
+typedef struct fstat_ephem {
+  double au_m, year_s, sidereal_day_s, obliquity_rad, orb_phase0, sid_phase0;
+} fstat_ephem;
+
+/* Everything fixed for a plan.  dt: sampling time of x_h (s); t_start: time
+ * of x_h[0] and reference time of the heterodyne and spindown phases;
+ * n_data: samples of x_h; f_het: heterodyne frequency f_h (Hz); sigma2:
+ * E|n|^2 of one complex noise sample; n_fft: FFT length (power of two,
+ * 2^12..2^24); interp/taps/window: step 4 (taps even, 2..16, used by SINC);
+ * precision: FSTAT_PREC_*; max_templates: largest n_t of one call. */
+typedef struct fstat_plan_desc {
+  double dt;
+  double t_start;
+  int64_t n_data;
+  double f_het;
+  double sigma2;
+  int64_t n_fft;
+  int32_t interp;
+  int32_t taps;
+  int32_t window;
+  int32_t precision;
+  fstat_detector det;
+  fstat_ephem eph;
+  int64_t max_templates;
+} fstat_plan_desc;
+
+/* One template.  span_start/span_len: the data samples it uses
+ * [span_start, span_start + span_len); gap_off/n_gaps: its gap intervals
+ * gaps[2*gap_off .. 2*(gap_off+n_gaps)) as sorted, disjoint [start, end)
+ * sample pairs inside the span; n_fft: 0 for the plan's n_fft, else a power
+ * of two <= the plan's (persistent mode only); out_off: offset of its 2F
+ * values in the output array in floats, -1 for index * plan n_fft. */
+typedef struct fstat_template {
+  double alpha, delta, fdot;
+  int64_t span_start, span_len;
+  int64_t gap_off, n_gaps;
+  int64_t n_fft, out_off;
+} fstat_template;
+
+/* Kernel shape choices (set by the autotuner; zeros mean automatic).
+ * log2_n1: log2 of the first-pass (column) FFT length; cols: columns per
+ * block in the first pass; rows: rows per block in the second pass; chunk:
+ * templates per internal batch; knot_log2: log2 of the knot spacing of the
+ * time map in samples. */
+typedef struct fstat_tuning {
+  int32_t mode;
+  int32_t log2_n1;
+  int32_t cols;
+  int32_t rows;
+  int32_t chunk;
+  int32_t knot_log2;
+} fstat_tuning;
+
+typedef struct fstat_plan_s *fstat_plan_t;
+
+/* Create a plan (allocates its twiddle tables and status word on the current
+ * device) and report the workspace size needed for max_templates templates
+ * at the default tuning.  Errors: EINVAL (null pointer, dt <= 0, sigma2 <= 0,
+ * n_data < 2, bad enum), ERANGE (n_fft not a power of two in 2^12..2^24,
+ * |f_het dt| > 1e6), ENOTSUP (taps outside 2..16 or odd), ENOMEM, ECUDA. */
+int fstat_plan(fstat_plan_t *out, const fstat_plan_desc *d, size_t *workspace_bytes);
+
+/* Change the kernel shapes / mode; reports the new workspace size.  The
+ * current workspace is dropped if it is now too small. */
+int fstat_set_tuning(fstat_plan_t p, const fstat_tuning *t, size_t *workspace_bytes);
+int fstat_get_tuning(fstat_plan_t p, fstat_tuning *t);
+
+/* Attach caller-owned device scratch of at least the reported size (256-byte
+ * aligned).  The library zeroes its counters with cudaMemset. */
+int fstat_set_workspace(fstat_plan_t p, void *dev_ptr, size_t bytes);
+
+/* Host helper: resampled length N_b of each template (host arrays), the
+ * number of points of the uniform barycentric grid (Eq. 21).  A template
+ * with an invalid span gets N_b = -1. */
+int fstat_template_nb(fstat_plan_t p, const fstat_template *host_t, int64_t n_t,
+                      int64_t *host_nb);
+
+/* Steps 1-5 only (debug/parity stage): writes the weighted series
+ * wa = m a z e^{-2 pi i (f_h tau + fdot tau_b^2/2)} and wb (complex64,
+ * interleaved re/im, [n_t][n_fft], zero beyond N_b) and abcd[n_t][4] =
+ * (A, B, C, D) in float64.  x_h: complex64 [n_data] (8-byte aligned);
+ * templates: device [n_t]; gaps: device int64 [2 * n_gaps_total]. */
+int fstat_resample(fstat_plan_t p, const float *x_h, const fstat_template *templates,
+                   int64_t n_t, const int64_t *gaps, int64_t n_gaps_total,
+                   float *wa, float *wb, double *abcd, void *stream);
+
+/* Steps 1-7: 2F in every bin, float32, twoF[out_off + q] per template.  All
+ * pointers device; the output array must hold every template's n_fft
+ * values at its offset. */
+int fstat_compute(fstat_plan_t p, const float *x_h, const fstat_template *templates,
+                  int64_t n_t, const int64_t *gaps, int64_t n_gaps_total,
+                  float *twoF, void *stream);
+
+/* 2F of the resampled series at one continuous frequency offset df[i] per
+ * template (the DFT of Eqs. 19-20 evaluated off the FFT grid) and its
+ * gradient with respect to (alpha, delta, f, fdot), computed by a forward
+ * pass and an adjoint pass over the samples.  Needs FSTAT_SINC (the
+ * nearest-neighbour series is piecewise constant in the template).
+ * df: device float64 [n_t]; twoF: device float64 [n_t]; grad: device
+ * float64 [n_t][4]. */
+int fstat_grad(fstat_plan_t p, const float *x_h, const fstat_template *templates,
+               const double *df, int64_t n_t, const int64_t *gaps, int64_t n_gaps_total,
+               double *twoF, double *grad, void *stream);
+
+/* Per-kernel timing.  While enabled, the library records a CUDA event pair
+ * on the call's stream around every kernel it launches.  fstat_profile_read
+ * waits for the recorded events and returns, per kernel kind (0 time map,
+ * 1 resample stage, 2 first FFT pass, 3 second FFT pass, 4 gradient
+ * forward, 5 gradient adjoint, 6 persistent batch), the summed device
+ * milliseconds and the number of launches since the last read, then clears
+ * them.  Launch counts are kept whether or not timing is enabled.  ms and
+ * launches are host arrays of n_kinds entries (n_kinds <= 8). */
+int fstat_profile(fstat_plan_t p, int enable);
+int fstat_profile_read(fstat_plan_t p, double *ms, int64_t *launches, int n_kinds);
+
+/* Synchronise the stream, return and clear the first device-side error
+ * recorded since the last call (FSTAT_OK if none). */
+int fstat_status(fstat_plan_t p, void *stream);
+
+/* Free the plan's own allocations (not the workspace). NULL is a no-op. */
+void fstat_destroy(fstat_plan_t p);
+
+/* Text of a status code. */
+const char *fstat_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSTAT_H */

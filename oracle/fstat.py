@@ -141,6 +141,17 @@ def single_bin_two_f(x_h, tmpl, gaps, plan, df):
     return float(two_f(Fa, Fb, r["A"], r["B"], r["C"], plan.sigma2))
 
 
+def single_bin_two_f_many(x_h, tmpl, gaps, plan, dfs):
+    """``single_bin_two_f`` at several frequency offsets (series computed once)."""
+    r = resampled_series(x_h, tmpl, gaps, plan)
+    tau_b = r["tb"] - plan.t_start
+    out = np.empty(len(dfs))
+    for i, df in enumerate(dfs):
+        e = np.exp(-2j * np.pi * _frac(df * tau_b))
+        out[i] = two_f(np.sum(r["wa"] * e), np.sum(r["wb"] * e), r["A"], r["B"], r["C"], plan.sigma2)
+    return out
+
+
 def single_bin_gradient(x_h, tmpl, gaps, plan, df, steps=None):
     """d(2F)/d(alpha, delta, f, fdot) of ``single_bin_two_f`` by central
     differences with one Richardson extrapolation (FP64).  Default steps:

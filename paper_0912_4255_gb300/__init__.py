@@ -1,0 +1,233 @@
+"""GB300 barycentric-resampling F-statistic.
+
+Thin Python binding over ``libfstat.so`` (C ABI in ``include/fstat.h``).  The
+functions below carry the names of the C entry points and only marshal
+arguments: torch tensors provide device memory and streams, every step of
+the computation runs in the library's CUDA kernels.
+
+    plan = fstat_plan(desc)                  # desc: any object with the
+                                             # fstat_plan_desc fields
+    twoF = fstat_compute(plan, x_h, templates, gaps)
+    fstat_status(plan)                       # raises on a device-side error
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (MODE_FUSED, MODE_PERSISTENT, MODE_PLAIN, NEAREST, PREC_FP32, PREC_FP64,
+                   PREC_MIXED, SINC, TEMPLATE_DTYPE, WIN_LANCZOS, WIN_RECT)
+
+__all__ = [
+    "FstatError", "Plan", "fstat_plan", "fstat_compute", "fstat_resample", "fstat_grad",
+    "fstat_status", "fstat_destroy", "fstat_strerror", "fstat_template_nb", "pack_templates",
+    "fstat_profile", "fstat_profile_read", "KERNEL_KINDS",
+    "NEAREST", "SINC", "WIN_RECT", "WIN_LANCZOS", "PREC_MIXED", "PREC_FP64", "PREC_FP32",
+    "MODE_FUSED", "MODE_PLAIN", "MODE_PERSISTENT", "TEMPLATE_DTYPE",
+]
+
+
+class FstatError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        self.code = code
+        super().__init__(f"{where}: {fstat_strerror(code)} ({code})")
+
+
+def fstat_strerror(code: int) -> str:
+    return _lib.load().fstat_strerror(int(code)).decode()
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise FstatError(rc, where)
+
+
+def _desc(d) -> _lib.PlanDesc:
+    """fstat_plan_desc from any object carrying the same field names."""
+    det = _lib.Detector(d.det.lat_rad, d.det.lon_rad, d.det.gamma_rad, d.det.radius_m)
+    eph = _lib.Ephem(d.eph.au_m, d.eph.year_s, d.eph.sidereal_day_s, d.eph.obliquity_rad,
+                     d.eph.orb_phase0, d.eph.sid_phase0)
+    return _lib.PlanDesc(float(d.dt), float(d.t_start), int(d.n_data), float(d.f_het),
+                         float(d.sigma2), int(d.n_fft), int(d.interp), int(d.taps),
+                         int(d.window), int(d.precision), det, eph, int(d.max_templates))
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def pack_templates(templates, device="cuda"):
+    """Upload templates (a structured array with the fstat_template fields,
+    or a sequence of dicts) as a device tensor of raw fstat_template
+    records."""
+    import torch
+    arr = np.zeros(len(templates), dtype=TEMPLATE_DTYPE)
+    for name in TEMPLATE_DTYPE.names:
+        if isinstance(templates, np.ndarray) and templates.dtype.names:
+            if name in templates.dtype.names:
+                arr[name] = templates[name]
+            elif name == "out_off":
+                arr[name] = -1
+        else:
+            arr[name] = [t.get(name, -1 if name == "out_off" else 0) for t in templates]
+    raw = torch.from_numpy(arr.view(np.uint8).copy())
+    return raw.to(device) if device is not None else raw
+
+
+class Plan:
+    """Owner of an fstat plan and of its torch-allocated workspace."""
+
+    def __init__(self, desc, device=None):
+        import torch
+        self.lib = _lib.load()
+        self.device = torch.device("cuda" if device is None else device)
+        self.desc = desc
+        h = ctypes.c_void_p()
+        need = ctypes.c_size_t()
+        with torch.cuda.device(self.device):
+            _check(self.lib.fstat_plan(ctypes.byref(h), ctypes.byref(_desc(desc)), ctypes.byref(need)),
+                   "fstat_plan")
+        self.handle = h
+        self.workspace = None
+        self._attach(need.value)
+
+    def _attach(self, nbytes: int):
+        import torch
+        if self.workspace is not None and self.workspace.numel() >= nbytes:
+            ws = self.workspace
+        else:
+            self.workspace = None
+            ws = torch.empty(max(nbytes, 256) + 256, dtype=torch.uint8, device=self.device)
+        off = (-ws.data_ptr()) % 256
+        self.workspace = ws
+        _check(self.lib.fstat_set_workspace(self.handle, ctypes.c_void_p(ws.data_ptr() + off),
+                                            ws.numel() - off), "fstat_set_workspace")
+
+    def set_tuning(self, mode=MODE_FUSED, log2_n1=0, cols=0, rows=0, chunk=0, knot_log2=0):
+        need = ctypes.c_size_t()
+        t = _lib.Tuning(mode, log2_n1, cols, rows, chunk, knot_log2)
+        _check(self.lib.fstat_set_tuning(self.handle, ctypes.byref(t), ctypes.byref(need)),
+               "fstat_set_tuning")
+        self._attach(need.value)
+
+    def tuning(self) -> dict:
+        t = _lib.Tuning()
+        _check(self.lib.fstat_get_tuning(self.handle, ctypes.byref(t)), "fstat_get_tuning")
+        return {n: getattr(t, n) for n, _ in _lib.Tuning._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.fstat_destroy(self.handle)
+            self.handle = None
+        self.workspace = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fstat_plan(desc, device=None) -> Plan:
+    return Plan(desc, device)
+
+
+def fstat_destroy(plan: Plan):
+    plan.close()
+
+
+def _n_templates(templates) -> int:
+    return templates.numel() // TEMPLATE_DTYPE.itemsize
+
+
+def _gap_args(gaps):
+    if gaps is None or gaps.numel() == 0:
+        return ctypes.c_void_p(0), 0
+    assert gaps.dtype.itemsize == 8 and gaps.is_cuda
+    return _ptr(gaps), gaps.numel() // 2
+
+
+def fstat_compute(plan: Plan, x_h, templates, gaps=None, twoF=None, stream=None):
+    """2F for every template and bin (float32, [n_templates * n_fft] unless
+    templates carry their own offsets)."""
+    import torch
+    assert x_h.is_cuda and x_h.dtype == torch.complex64 and x_h.is_contiguous()
+    n_t = _n_templates(templates)
+    if twoF is None:
+        twoF = torch.empty(n_t * int(plan.desc.n_fft), dtype=torch.float32, device=x_h.device)
+    g, ng = _gap_args(gaps)
+    _check(plan.lib.fstat_compute(plan.handle, _ptr(x_h), _ptr(templates), n_t, g, ng,
+                                  _ptr(twoF), _stream(stream)), "fstat_compute")
+    return twoF
+
+
+def fstat_resample(plan: Plan, x_h, templates, gaps=None, stream=None):
+    """Steps 1-5 only: (wa, wb, abcd) with wa, wb complex64 [n_t, n_fft]."""
+    import torch
+    n_t = _n_templates(templates)
+    n = int(plan.desc.n_fft)
+    wa = torch.empty((n_t, n), dtype=torch.complex64, device=x_h.device)
+    wb = torch.empty_like(wa)
+    abcd = torch.empty((n_t, 4), dtype=torch.float64, device=x_h.device)
+    g, ng = _gap_args(gaps)
+    _check(plan.lib.fstat_resample(plan.handle, _ptr(x_h), _ptr(templates), n_t, g, ng,
+                                   _ptr(wa), _ptr(wb), _ptr(abcd), _stream(stream)), "fstat_resample")
+    return wa, wb, abcd
+
+
+def fstat_grad(plan: Plan, x_h, templates, df, gaps=None, stream=None):
+    """2F at df (float64 [n_t]) and d2F/d(alpha, delta, f, fdot) ([n_t, 4])."""
+    import torch
+    n_t = _n_templates(templates)
+    twoF = torch.empty(n_t, dtype=torch.float64, device=x_h.device)
+    grad = torch.empty((n_t, 4), dtype=torch.float64, device=x_h.device)
+    g, ng = _gap_args(gaps)
+    df = df.to(device=x_h.device, dtype=torch.float64).contiguous()
+    _check(plan.lib.fstat_grad(plan.handle, _ptr(x_h), _ptr(templates), _ptr(df), n_t, g, ng,
+                               _ptr(twoF), _ptr(grad), _stream(stream)), "fstat_grad")
+    return twoF, grad
+
+
+KERNEL_KINDS = ("timemap", "resample", "fft_cols", "fft_rows", "grad_fwd", "grad_adj", "persistent")
+
+
+def fstat_profile(plan: Plan, enable: bool = True):
+    """Enable/disable CUDA-event timing of every kernel launch."""
+    _check(plan.lib.fstat_profile(plan.handle, int(bool(enable))), "fstat_profile")
+
+
+def fstat_profile_read(plan: Plan) -> dict:
+    """{kind: (milliseconds, launches)} since the last read (waits for the
+    recorded events)."""
+    n = len(KERNEL_KINDS)
+    ms = (ctypes.c_double * n)()
+    ln = (ctypes.c_int64 * n)()
+    _check(plan.lib.fstat_profile_read(plan.handle, ms, ln, n), "fstat_profile_read")
+    return {k: (ms[i], ln[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+
+def fstat_status(plan: Plan, stream=None, raise_error=True) -> int:
+    rc = plan.lib.fstat_status(plan.handle, _stream(stream))
+    if rc and raise_error:
+        raise FstatError(rc, "device status")
+    return rc
+
+
+def fstat_template_nb(plan: Plan, templates_np) -> np.ndarray:
+    """Resampled length N_b of each template (host computation)."""
+    arr = np.ascontiguousarray(templates_np.astype(TEMPLATE_DTYPE) if templates_np.dtype != TEMPLATE_DTYPE
+                               else templates_np)
+    out = np.zeros(len(arr), dtype=np.int64)
+    _check(plan.lib.fstat_template_nb(plan.handle, arr.ctypes.data_as(ctypes.POINTER(_lib.Template)),
+                                      len(arr), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
+           "fstat_template_nb")
+    return out

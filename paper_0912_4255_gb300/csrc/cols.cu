@@ -1,0 +1,45 @@
+// First FFT pass instantiations for one (precision, log2 N1), selected at
+// build time by FS_REAL (float|double) and FS_L1 (6..12); the build compiles
+// this file once per pair so that the units compile in parallel.
+#include "passes.cuh"
+
+#ifndef FS_REAL
+#define FS_REAL float
+#endif
+#ifndef FS_L1
+#define FS_L1 11
+#endif
+
+#define FS_CAT2(a, b, c) a##_##b##_##c
+#define FS_CAT(a, b, c) FS_CAT2(a, b, c)
+
+namespace fs {
+
+namespace {
+template <typename R, int L1, int SRC, int TAPS>
+cudaError_t run(const ColsArgs<R>& a, dim3 grid, cudaStream_t s) {
+  constexpr int C = cols_for<R>(L1);
+  constexpr int NT = threads_for<R>(L1, 2 * C);
+  constexpr size_t SM = smem_for<R, L1, 2 * C>();
+  auto kern = k_cols<R, L1, C, NT, SRC, TAPS>;
+  static int attr_done = 0;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM);
+    if (e != cudaSuccess) return e;
+    attr_done = 1;
+  }
+  kern<<<grid, NT, SM, s>>>(a);
+  return cudaGetLastError();
+}
+}  // namespace
+
+// src: SRC_LOAD / SRC_NN / SRC_SINC; taps8: compiled 8-tap path
+cudaError_t FS_CAT(cols, FS_REAL, FS_L1)(const ColsArgs<FS_REAL>& a, int src, int taps8, dim3 grid, cudaStream_t s) {
+  if (src == SRC_LOAD) return run<FS_REAL, FS_L1, SRC_LOAD, 8>(a, grid, s);
+  if (src == SRC_NN) return run<FS_REAL, FS_L1, SRC_NN, 8>(a, grid, s);
+  if (taps8) return run<FS_REAL, FS_L1, SRC_SINC, 8>(a, grid, s);
+  return run<FS_REAL, FS_L1, SRC_SINC, 0>(a, grid, s);
+}
+int FS_CAT(colsC, FS_REAL, FS_L1)() { return cols_for<FS_REAL>(FS_L1); }
+
+}  // namespace fs

@@ -1,0 +1,594 @@
+// Internal declarations of the F-statistic library: plan constants, the
+// per-template metadata, knot records of the time map, device math helpers
+// and the shared-memory Stockham FFT used by both FFT passes.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "../../include/fstat.h"
+
+namespace fs {
+
+// ---------------------------------------------------------------- constants
+
+constexpr double kC = 299792458.0;        // speed of light, m/s
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr int kTwLog = 12;                // twiddle tables split at 2^12
+constexpr int kTwLo = 1 << kTwLog;
+constexpr int kMaxLog = 24;               // largest FFT: 2^24
+constexpr int kMinLog = 12;               // smallest FFT: 2^12
+
+// Plan constants passed by value to every kernel.
+struct PlanConst {
+  double dt, t_start, f_het, sigma2;
+  int64_t n_data;
+  int32_t interp, taps, window, precision;
+  double lat, lon, gamma, radius;                 // detector
+  double au, year, sid, obliq, orb0, sid0;        // ephemeris
+  int32_t log2h;                                  // knot spacing (samples)
+  int32_t pad_;
+};
+
+// Per-template state produced by the time-map kernel and completed by the
+// first FFT pass (sums A, B, C and the 2F coefficients).
+struct TmplMeta {
+  double tb0;        // t_b of grid point 0
+  double A, B, C;    // masked antenna sums (Eq. 9 as sums)
+  int64_t n_b;       // resampled length N_b
+  int64_t out_off;   // output offset in floats
+  int64_t span_lo, span_hi, gap_off, n_gaps;
+  int32_t n_int;     // knot intervals
+  int32_t log2n;     // FFT length of this template
+  int32_t status;    // FSTAT_OK or the error of this template
+  float ca, cb, cc;  // 2F = ca |Fa|^2 + cb |Fb|^2 + cc Re(Fa Fb*)
+  int32_t pad_;
+};
+
+// Knot interval record, single precision evaluation (80 bytes).  On the
+// interval [k_j, k_j + h) with s = k - k_j:
+//   u(s)     = I + s + F + ((u3 s + u2) s + u1) s      fractional data index
+//   P(s)     = P + ((p3 s + p2) s + p1) s              phase to remove, cycles
+//   a(s)     = a0 + ((a3 s + a2) s + a1) s             beam pattern a(T^k)
+//   b(s)     = b0 + ((b3 s + b2) s + b1) s
+// I is exact, F = frac(U_j) and P = frac(P_j) are reduced in FP64, so only
+// small deviations are carried in FP32.
+struct __align__(16) KnotF {
+  int32_t I; float F, u1, u2;
+  float u3, P, p1, p2;
+  float p3, a0, a1, a2;
+  float a3, b0, b1, b2;
+  float b3, r0, r1, r2;
+};
+// Double precision record (128 bytes); U is the full fractional index.
+struct __align__(16) KnotD {
+  double U, u1, u2, u3;
+  double P, p1, p2, p3;
+  double a0, a1, a2, a3;
+  double b0, b1, b2, b3;
+};
+
+template <typename R> struct Cx;
+template <> struct Cx<float> { using T = float2; };
+template <> struct Cx<double> { using T = double2; };
+template <typename R> using cpx = typename Cx<R>::T;
+
+template <typename R> struct KnotOf;
+template <> struct KnotOf<float> { using T = KnotF; };
+template <> struct KnotOf<double> { using T = KnotD; };
+
+// Twiddle tables: tl[L][m] = exp(-2 pi i m / 2^L) for m < min(2^L, 4096);
+// th[L][m] = exp(-2 pi i m 4096 / 2^L) for L > 12, m < 2^(L-12).
+template <typename R> struct Tw {
+  const cpx<R>* tl[kMaxLog + 1];
+  const cpx<R>* th[kMaxLog + 1];
+};
+
+// ---------------------------------------------------------------- complex
+
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+template <typename T> __host__ __device__ __forceinline__ T czero();
+template <> __host__ __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
+template <> __host__ __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+template <typename T, typename S> __host__ __device__ __forceinline__ T cmk(S re, S im);
+template <> __host__ __device__ __forceinline__ float2 cmk<float2, float>(float re, float im) { return make_float2(re, im); }
+template <> __host__ __device__ __forceinline__ double2 cmk<double2, double>(double re, double im) { return make_double2(re, im); }
+
+// multiply by -i (used by the in-register butterflies)
+__device__ __forceinline__ float2 cmul_mi(float2 a) { return make_float2(a.y, -a.x); }
+__device__ __forceinline__ double2 cmul_mi(double2 a) { return make_double2(a.y, -a.x); }
+
+// ---------------------------------------------------------------- status
+
+__device__ __forceinline__ void set_status(int* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+// ---------------------------------------------------------------- geometry
+// Roemer delay t_m = n.r_d/c (Eq. 4pt2) and its rate n.v_d/c (Eq. 11c) for
+// the analytic ephemeris, plus the JKS beam patterns a, b (Eqs. 2-3) in
+// coefficient form a = e0 + e1 cos x + e2 sin x + e3 cos 2x + e4 sin 2x,
+// b = f1 cos x + f2 sin x + f3 cos 2x + f4 sin 2x, x = alpha - theta(t).
+
+template <typename R>
+struct Sky {
+  R nx, ny, nz;                 // unit vector to the source
+  R ox, oy;                     // n . (cos phi, sin phi cos eps + ...) orbital projections
+  R rz;                         // R sin(lat) nz / c
+  R rxy;                        // R cos(lat) cos(delta) / c
+  R alpha;
+  R e0, e1, e2, e3, e4, f1, f2, f3, f4;
+};
+
+template <typename R>
+__device__ __forceinline__ Sky<R> make_sky(const PlanConst& pc, R alpha, R delta) {
+  Sky<R> s;
+  R sa, ca, sd, cd;
+  if constexpr (std::is_same<R, float>::value) { sincosf(alpha, &sa, &ca); sincosf(delta, &sd, &cd); }
+  else { sincos(alpha, &sa, &ca); sincos(delta, &sd, &cd); }
+  s.nx = cd * ca; s.ny = cd * sa; s.nz = sd;
+  const R ce = (R)cos(pc.obliq), se = (R)sin(pc.obliq);
+  const R auc = (R)(pc.au / kC);
+  s.ox = auc * s.nx;                         // coefficient of cos(phi)
+  s.oy = auc * (ce * s.ny + se * s.nz);      // coefficient of sin(phi)
+  const R sl = (R)sin(pc.lat), cl = (R)cos(pc.lat);
+  s.rz = (R)(pc.radius / kC) * sl * sd;
+  s.rxy = (R)(pc.radius / kC) * cl * cd;
+  s.alpha = alpha;
+  const R s2g = (R)sin(2 * pc.gamma), c2g = (R)cos(2 * pc.gamma);
+  const R c2l = (R)cos(2 * pc.lat), s2l = (R)sin(2 * pc.lat);
+  const R c2d = cd * cd - sd * sd, s2d = 2 * sd * cd;
+  s.e3 = s2g * (3 - c2l) * (3 - c2d) / 16;
+  s.e4 = -c2g * sl * (3 - c2d) / 4;
+  s.e1 = s2g * s2l * s2d / 4;
+  s.e2 = -c2g * cl * s2d / 2;
+  s.e0 = (R)0.75 * s2g * cl * cl * cd * cd;
+  s.f3 = c2g * sl * sd;
+  s.f4 = s2g * (3 - c2l) * sd / 4;
+  s.f1 = c2g * cl * cd;
+  s.f2 = s2g * s2l * cd / 2;
+  return s;
+}
+
+template <typename R>
+__device__ __forceinline__ void rsincos(R x, R* s, R* c) {
+  if constexpr (std::is_same<R, float>::value) sincosf(x, s, c); else sincos(x, s, c);
+}
+
+// t_m(t) and dt_m/dt.
+template <typename R>
+__device__ __forceinline__ void roemer(const PlanConst& pc, const Sky<R>& s, R t, R* tm, R* rate) {
+  const R wo = (R)(kTwoPi / pc.year), ws = (R)(kTwoPi / pc.sid);
+  R sp, cp, st, ct;
+  rsincos<R>((R)pc.orb0 + wo * t, &sp, &cp);
+  // hour-angle form: n . r_rot = R cos(lat) cos(delta) cos(theta - alpha) + R sin(lat) sin(delta)
+  rsincos<R>((R)(pc.sid0 + pc.lon) + ws * t - s.alpha, &st, &ct);
+  *tm = s.ox * cp + s.oy * sp + s.rxy * ct + s.rz;
+  *rate = wo * (s.oy * cp - s.ox * sp) - ws * s.rxy * st;
+}
+
+// a, b and their time derivatives at detector time t.
+template <typename R>
+__device__ __forceinline__ void beams(const PlanConst& pc, const Sky<R>& s, R t,
+                                      R* a, R* b, R* da, R* db) {
+  const R ws = (R)(kTwoPi / pc.sid);
+  R sx, cx;
+  rsincos<R>(s.alpha - ((R)(pc.sid0 + pc.lon) + ws * t), &sx, &cx);
+  const R c2x = cx * cx - sx * sx, s2x = 2 * sx * cx;
+  *a = s.e0 + s.e1 * cx + s.e2 * sx + s.e3 * c2x + s.e4 * s2x;
+  *b = s.f1 * cx + s.f2 * sx + s.f3 * c2x + s.f4 * s2x;
+  // dx/dt = -ws
+  *da = -ws * (-s.e1 * sx + s.e2 * cx - 2 * s.e3 * s2x + 2 * s.e4 * c2x);
+  *db = -ws * (-s.f1 * sx + s.f2 * cx - 2 * s.f3 * s2x + 2 * s.f4 * c2x);
+}
+
+// Detector time T with T + t_m(T) = tb (Eq. 21), by Newton's method started
+// from tb - t_m(tb); |dt_m/dt| <~ 1e-4 makes two steps exact to rounding.
+template <typename R>
+__device__ __forceinline__ R inverse_time(const PlanConst& pc, const Sky<R>& s, R tb) {
+  R tm, rate;
+  roemer<R>(pc, s, tb, &tm, &rate);
+  R T = tb - tm;
+#pragma unroll
+  for (int it = 0; it < 3; ++it) {
+    roemer<R>(pc, s, T, &tm, &rate);
+    T -= (T + tm - tb) / (1 + rate);
+  }
+  return T;
+}
+
+// ---------------------------------------------------------------- samples
+
+// Read a complex64 sample as R-precision complex.
+template <typename R>
+__device__ __forceinline__ cpx<R> ldx(const float2* __restrict__ x, int64_t j) {
+  const float2 v = __ldg(x + j);
+  return cmk<cpx<R>, R>((R)v.x, (R)v.y);
+}
+
+// Validity of data sample j for a template: inside its span and outside its
+// gaps.  ``g`` is a cursor into the sorted gap list, advanced monotonically
+// as the queried j increase.
+struct GapCursor {
+  const int64_t* __restrict__ gaps;  // pairs [start, end)
+  int64_t n, g;
+  int64_t lo, hi;
+  __device__ __forceinline__ void seek(int64_t j) {
+    // first gap whose end is > j (binary search)
+    int64_t a = 0, b = n;
+    while (a < b) {
+      const int64_t m = (a + b) >> 1;
+      if (__ldg(gaps + 2 * m + 1) <= j) a = m + 1; else b = m;
+    }
+    g = a;
+  }
+  __device__ __forceinline__ bool valid(int64_t j) {
+    if (j < lo || j >= hi) return false;
+    while (g < n && __ldg(gaps + 2 * g + 1) <= j) ++g;
+    return !(g < n && __ldg(gaps + 2 * g) <= j);
+  }
+};
+
+// Per-sample time map and weights (steps 2-5) at grid point k < N_b of a
+// template: returns the mask and writes wa = m a y, wb = m b y with
+// y = z(T^k) exp(-2 pi i P(k)), and the beam values a, b.
+template <typename R, int INTERP, int TAPS>
+__device__ __forceinline__ bool sample_weights(
+    const PlanConst& pc, const TmplMeta& m, const typename KnotOf<R>::T* __restrict__ kn,
+    int64_t k, const float2* __restrict__ x, const int64_t* __restrict__ gaps,
+    const double* __restrict__ wcs, cpx<R>& wa, cpx<R>& wb, R& a, R& b) {
+  using C = cpx<R>;
+  const int64_t jint = k >> pc.log2h;
+  const R s = (R)(k & ((1 << pc.log2h) - 1));
+  int64_t ibase;   // integer part of u before the deviation
+  R dev;           // u = ibase + dev
+  R ph;            // phase cycles
+  if constexpr (std::is_same<R, float>::value) {
+    const float4* q = reinterpret_cast<const float4*>(kn + jint);
+    const float4 r0 = __ldg(q), r1 = __ldg(q + 1), r2 = __ldg(q + 2), r3 = __ldg(q + 3), r4 = __ldg(q + 4);
+    ibase = (int64_t)__float_as_int(r0.x) + (k & ((1 << pc.log2h) - 1));
+    dev = r0.y + ((r1.x * s + r0.w) * s + r0.z) * s;
+    ph = r1.y + ((r2.x * s + r1.w) * s + r1.z) * s;
+    a = r2.y + ((r3.x * s + r2.w) * s + r2.z) * s;
+    b = r3.y + ((r4.x * s + r3.w) * s + r3.z) * s;
+  } else {
+    const KnotD& q = kn[jint];
+    const double u = q.U + s + ((q.u3 * s + q.u2) * s + q.u1) * s;
+    const double fl = floor(u);
+    ibase = (int64_t)fl;
+    dev = u - fl;
+    ph = q.P + ((q.p3 * s + q.p2) * s + q.p1) * s;
+    a = q.a0 + ((q.a3 * s + q.a2) * s + q.a1) * s;
+    b = q.b0 + ((q.b3 * s + q.b2) * s + q.b1) * s;
+  }
+  GapCursor gc{gaps, m.n_gaps, 0, m.span_lo, m.span_hi};
+  const int64_t jnn = ibase + (int64_t)floor(dev + (R)0.5);
+  C z;
+  if constexpr (INTERP == FSTAT_NEAREST) {
+    gc.seek(jnn);
+    if (!gc.valid(jnn)) { wa = czero<C>(); wb = czero<C>(); return false; }
+    z = ldx<R>(x, jnn);
+  } else {
+    const int taps = TAPS > 0 ? TAPS : pc.taps;
+    const int half = taps >> 1;
+    const R fl = floor(dev);
+    const int64_t n0 = ibase + (int64_t)fl;
+    // offset from the nearest sample, dn = u - jnn in [-1/2, 1/2]; every
+    // weight is formed from sin/cos of pi dn and pi dn / H, so the tap next
+    // to u gets its value without cancellation and the others have |x| >= 1/2
+    const R dn = dev - (R)(jnn - ibase);
+    gc.seek(n0 - half + 1);
+    if (dn == (R)0) {
+      bool ok = false;
+      for (int64_t j = n0 - half + 1; j <= jnn; ++j) ok = gc.valid(j);
+      if (!ok) { wa = czero<C>(); wb = czero<C>(); return false; }
+      z = ldx<R>(x, jnn);
+    } else {
+      // x = u - j = dn + mq with mq = jnn - j; sin(pi x) = (-1)^mq sin(pi dn);
+      // sin(pi x / H) = sin(pi dn/H) cos(pi mq/H) + cos(pi dn/H) sin(pi mq/H)
+      R S, Cd, sh, chh;
+      if constexpr (std::is_same<R, float>::value) {
+        sincospif(dn, &S, &Cd);
+        sincospif(dn / (R)half, &sh, &chh);
+      } else {
+        sincospi(dn, &S, &Cd);
+        sincospi(dn / (R)half, &sh, &chh);
+      }
+      const R inv_pi2 = (R)(1.0 / (3.14159265358979323846 * 3.14159265358979323846));
+      const bool lanczos = pc.window == FSTAT_WIN_LANCZOS;
+      const int qoff = (int)(jnn - n0);          // 0 or 1
+      C acc = czero<C>();
+      bool msk = false;
+#pragma unroll
+      for (int i = 0; i < (TAPS > 0 ? TAPS : 16); ++i) {
+        if (TAPS == 0 && i >= taps) break;
+        const int mq = half - 1 - i + qoff;       // jnn - j
+        const int64_t j = n0 + 1 - half + i;
+        const R xx = dn + (R)mq;
+        R w = S * inv_pi2 / (xx * xx);
+        if (mq & 1) w = -w;
+        if (lanczos) {
+          w *= (R)half * (sh * (R)wcs[2 * (mq + half)] + chh * (R)wcs[2 * (mq + half) + 1]);
+        } else {
+          w *= (R)3.14159265358979323846 * xx;   // plain truncated sinc: sin(pi x)/(pi x)
+        }
+        const bool ok = gc.valid(j);
+        if (j == jnn) msk = ok;
+        if (ok) {
+          const C v = ldx<R>(x, j);
+          acc.x = fma(w, v.x, acc.x);
+          acc.y = fma(w, v.y, acc.y);
+        }
+      }
+      if (!msk) { wa = czero<C>(); wb = czero<C>(); return false; }
+      z = acc;
+    }
+  }
+  // remove exp(2 pi i P): multiply by exp(-2 pi i r), r = P - rint(P)
+  R r = ph - rint(ph);
+  R sp, cp;
+  if constexpr (std::is_same<R, float>::value) sincospif(2.f * r, &sp, &cp); else sincospi(2.0 * r, &sp, &cp);
+  const C e = cmk<C, R>(cp, -sp);
+  const C y = cmul(z, e);
+  wa = cmk<C, R>(a * y.x, a * y.y);
+  wb = cmk<C, R>(b * y.x, b * y.y);
+  return true;
+}
+
+// ---------------------------------------------------------------- FFT
+// In-register DFT of RAD points (forward, e^{-2 pi i jk/RAD}) by radix-2
+// decimation in time; twiddles are compile-time constants.
+
+// cos and sin of 2 pi k / 16 for k = 0..15
+__host__ __device__ constexpr double c16(int k) {
+  return k == 0 ? 1.0 : k == 1 ? 0.92387953251128675613 : k == 2 ? 0.70710678118654752440
+       : k == 3 ? 0.38268343236508977173 : k == 4 ? 0.0 : k == 5 ? -0.38268343236508977173
+       : k == 6 ? -0.70710678118654752440 : k == 7 ? -0.92387953251128675613 : k == 8 ? -1.0
+       : k == 9 ? -0.92387953251128675613 : k == 10 ? -0.70710678118654752440
+       : k == 11 ? -0.38268343236508977173 : k == 12 ? 0.0 : k == 13 ? 0.38268343236508977173
+       : k == 14 ? 0.70710678118654752440 : 0.92387953251128675613;
+}
+__host__ __device__ constexpr double s16(int k) { return c16((k + 12) & 15); }  // sin(2 pi k/16) = cos(2 pi (k-4)/16)
+
+template <typename T, int RAD, int STRIDE = 1>
+struct Dft {
+  // v[0], v[STRIDE], ... hold the RAD inputs; outputs in natural order at the same slots
+  __device__ __forceinline__ static void run(T* v) {
+    if constexpr (RAD == 1) {
+      return;
+    } else {
+      // even/odd split: evens at stride 2*STRIDE from 0, odds from STRIDE
+      Dft<T, RAD / 2, 2 * STRIDE>::run(v);
+      Dft<T, RAD / 2, 2 * STRIDE>::run(v + STRIDE);
+      T tmp[RAD];
+#pragma unroll
+      for (int k = 0; k < RAD / 2; ++k) {
+        const T e = v[2 * k * STRIDE];
+        T o = v[(2 * k + 1) * STRIDE];
+        constexpr int step = 16 / RAD;
+        const int kk = k * step;                // W_RAD^k = W_16^(k*16/RAD)
+        if (kk == 4) {
+          o = cmul_mi(o);
+        } else if (kk != 0) {
+          using R = decltype(o.x);
+          const T w = cmk<T, R>((R)c16(kk), (R)(-s16(kk)));
+          o = cmul(o, w);
+        }
+        tmp[k] = cadd(e, o);
+        tmp[k + RAD / 2] = csub(e, o);
+      }
+#pragma unroll
+      for (int k = 0; k < RAD; ++k) v[k * STRIDE] = tmp[k];
+    }
+  }
+};
+
+// padded shared-memory index: one extra element every 16 avoids bank
+// conflicts of the stride-16 writes of the first radix-16 stage
+__device__ __forceinline__ int pidx(int e) { return e + (e >> 4); }
+template <int LOGN> struct FftGeom {
+  static constexpr int N = 1 << LOGN;
+  static constexpr int STRIDE = N + (N >> 4) + 1;   // +1: columns start on different banks
+};
+
+// One Stockham stage of radix 2^RB over COUNT sequences of length 2^LOGN in
+// shared memory (sequence f at buf + f * STRIDE, padded); NS = 2^NSL is the
+// length of the sub-transforms already done.  Every thread handles UPT units
+// of 16 points; all reads happen before the barrier, all writes after it.
+template <typename R, int LOGN, int RB, int NSL, int NT, int COUNT>
+__device__ __forceinline__ void stockham_stage(cpx<R>* __restrict__ buf, const cpx<R>* __restrict__ tw) {
+  using C = cpx<R>;
+  constexpr int N = 1 << LOGN;
+  constexpr int RAD = 1 << RB;
+  constexpr int STRIDE = FftGeom<LOGN>::STRIDE;
+  constexpr int BPU = 16 / RAD;                   // butterflies per 16-point unit
+  constexpr int UNITS_PER_SEQ = N / 16;
+  constexpr int UNITS = COUNT * UNITS_PER_SEQ;
+  constexpr int UPT = (UNITS + NT - 1) / NT;
+  constexpr int NS = 1 << NSL;
+  C v[UPT][16];
+#pragma unroll
+  for (int u = 0; u < UPT; ++u) {
+    const int unit = threadIdx.x + u * NT;
+    if (UNITS % NT == 0 || unit < UNITS) {
+      const int f = unit / UNITS_PER_SEQ;
+      const int w = unit - f * UNITS_PER_SEQ;
+      const C* src = buf + f * STRIDE;
+#pragma unroll
+      for (int bb = 0; bb < BPU; ++bb) {
+        const int j = w * BPU + bb;
+        const int k = j & (NS - 1);
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) v[u][bb * RAD + r] = src[pidx(j + r * (N / RAD))];
+        if constexpr (NSL > 0) {
+#pragma unroll
+          for (int r = 1; r < RAD; ++r) {
+            const int mexp = (r * k) << (LOGN - NSL - RB);   // W_{NS RAD}^{r k} = W_N^{r k N/(NS RAD)}
+            v[u][bb * RAD + r] = cmul(v[u][bb * RAD + r], __ldg(tw + mexp));
+          }
+        }
+        Dft<C, RAD>::run(&v[u][bb * RAD]);
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < UPT; ++u) {
+    const int unit = threadIdx.x + u * NT;
+    if (UNITS % NT == 0 || unit < UNITS) {
+      const int f = unit / UNITS_PER_SEQ;
+      const int w = unit - f * UNITS_PER_SEQ;
+      C* dst = buf + f * STRIDE;
+#pragma unroll
+      for (int bb = 0; bb < BPU; ++bb) {
+        const int j = w * BPU + bb;
+        const int k = j & (NS - 1);
+        const int base = ((j >> NSL) << (NSL + RB)) + k;
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) dst[pidx(base + r * NS)] = v[u][bb * RAD + r];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Full FFT: radix-16 stages, then one stage of the remaining radix.
+template <typename R, int LOGN, int NSL, int NT, int COUNT>
+__device__ __forceinline__ void fft_stages(cpx<R>* buf, const cpx<R>* tw) {
+  if constexpr (NSL < LOGN) {
+    constexpr int REM = LOGN - NSL;
+    constexpr int RB = REM >= 4 ? 4 : REM;
+    stockham_stage<R, LOGN, RB, NSL, NT, COUNT>(buf, tw);
+    fft_stages<R, LOGN, NSL + RB, NT, COUNT>(buf, tw);
+  }
+}
+
+template <typename R, int LOGN, int NT, int COUNT>
+__device__ __forceinline__ void fft_smem(cpx<R>* buf, const cpx<R>* tw) {
+  fft_stages<R, LOGN, 0, NT, COUNT>(buf, tw);
+}
+
+// exp(-2 pi i m / 2^L) from the two-level tables
+template <typename R>
+__device__ __forceinline__ cpx<R> twiddle(const Tw<R>& tw, int L, uint32_t m) {
+  if (L <= kTwLog) return __ldg(tw.tl[L] + m);
+  return cmul(__ldg(tw.th[L] + (m >> kTwLog)), __ldg(tw.tl[L] + (m & (kTwLo - 1))));
+}
+
+// Block-wide sum of three doubles (any block size multiple of 32, <= 1024).
+__device__ __forceinline__ void block_sum3(double& x, double& y, double& z, double* sh /*[3*32]*/) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    x += __shfl_down_sync(0xffffffffu, x, o);
+    y += __shfl_down_sync(0xffffffffu, y, o);
+    z += __shfl_down_sync(0xffffffffu, z, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) { sh[wid] = x; sh[32 + wid] = y; sh[64 + wid] = z; }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    x = lane < nw ? sh[lane] : 0.0;
+    y = lane < nw ? sh[32 + lane] : 0.0;
+    z = lane < nw ? sh[64 + lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_down_sync(0xffffffffu, x, o);
+      y += __shfl_down_sync(0xffffffffu, y, o);
+      z += __shfl_down_sync(0xffffffffu, z, o);
+    }
+  }
+}
+
+// The last block of a template to finish its partial sums reduces them in
+// index order (deterministic) and fills A, B, C and the 2F coefficients.
+__device__ __forceinline__ void finalize_sums(TmplMeta* meta, const double* __restrict__ partials,
+                                              int nparts, int* counter, double sigma2, double* abcd,
+                                              int* status) {
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1) == nparts - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x == 0) {
+    double A = 0, B = 0, Cc = 0;
+    for (int i = 0; i < nparts; ++i) {
+      A += __ldcg(partials + 3 * i);
+      B += __ldcg(partials + 3 * i + 1);
+      Cc += __ldcg(partials + 3 * i + 2);
+    }
+    const double D = A * B - Cc * Cc;
+    meta->A = A; meta->B = B; meta->C = Cc;
+    if (!(D > 0.0) || !isfinite(D)) {       // no valid sample, or a and b proportional
+      meta->status = FSTAT_ERANGE;
+      set_status(status, FSTAT_ERANGE);
+    }
+    const double s = 1.0 / (sigma2 * D);
+    meta->ca = (float)(2.0 * B * s);
+    meta->cb = (float)(2.0 * A * s);
+    meta->cc = (float)(-4.0 * Cc * s);
+    if (abcd) { abcd[0] = A; abcd[1] = B; abcd[2] = Cc; abcd[3] = D; }
+    *counter = 0;
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+// (host side, defined in the .cu files)
+
+struct Chunk {
+  // one batch of templates: device pointers into the workspace
+  const fstat_template* tmpl;
+  TmplMeta* meta;
+  void* knots;            // [nt][knot_stride] records
+  int64_t knot_stride;    // records per template
+  double* partials;       // [nt][part_stride][3]
+  int64_t part_stride;
+  int* counters;          // [nt]
+  void* za;               // FFT intermediate [nt][2][n] complex (a plane, b plane)
+  int64_t z_stride;       // complex elements per template (2 n)
+  void* wa;               // plain path inputs [nt][2][n]
+  int nt;
+};
+
+struct Shape {
+  int log2n, l1, l2, cols, rows;
+};
+
+cudaError_t launch_timemap(const PlanConst& pc, const Chunk& c, int log2n_plan, int mode,
+                           const int64_t* gaps, int64_t n_gaps_total, int* status,
+                           int64_t tmpl_base, cudaStream_t s);
+cudaError_t launch_resample_w(const PlanConst& pc, const Chunk& c, int ti, int log2n, const float2* x,
+                              const int64_t* gaps, const double* wcs, void* out_a, void* out_b,
+                              int64_t out_stride, int out_double, double* abcd, int* status,
+                              cudaStream_t s);
+cudaError_t launch_cols_w(const PlanConst& pc, const Chunk& c, const Shape& sh, int fused, int ti,
+                          const float2* x, const int64_t* gaps, const double* wcs, const void* twf,
+                          const void* twd, int* status, cudaStream_t s);
+cudaError_t launch_rows_w(const PlanConst& pc, const Chunk& c, const Shape& sh, int ti, const void* twf,
+                          const void* twd, float* out, cudaStream_t s);
+cudaError_t launch_grad_pass(const PlanConst& pc, const Chunk& c, const float2* x, const int64_t* gaps,
+                             const double* wcs, const double* df, double* work, double* twoF,
+                             double* grad, int* status, int pass, cudaStream_t s);
+size_t grad_work_doubles(int nt);
+int cols_per_block(int precision, int l1);
+int rows_per_block(int precision, int l2);
+
+// Host copy of the t_b-grid computation (same formulas, FP64) used to size
+// work and by fstat_template_nb.
+int64_t host_nb(const PlanConst& pc, const fstat_template& t, double* tb0);
+
+}  // namespace fs

@@ -1,0 +1,107 @@
+"""The C ABI without a GPU: the library builds, exports every function the
+header declares, its structures have the header's layout, and host-side
+argument checks answer before any device work."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fstat.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_0912_4255_gb300 import build
+    build.build()
+    from paper_0912_4255_gb300 import _lib
+    return _lib.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fstat_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for n in ("fstat_plan", "fstat_set_workspace", "fstat_resample", "fstat_compute",
+              "fstat_grad", "fstat_status", "fstat_destroy", "fstat_strerror"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib._name], capture_output=True, text=True)
+    exported = set(re.findall(r"\bT (fstat_\w+)", out.stdout))
+    for n in declared_functions():
+        assert n in exported, n
+        assert getattr(lib, n) is not None
+
+
+def _c_layout():
+    """sizeof/offsetof of the header structures as the C compiler sees them."""
+    from paper_0912_4255_gb300 import _lib
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', 'int main(void){']
+    for cname, cls in (("fstat_detector", _lib.Detector), ("fstat_ephem", _lib.Ephem),
+                       ("fstat_plan_desc", _lib.PlanDesc), ("fstat_template", _lib.Template),
+                       ("fstat_tuning", _lib.Tuning)):
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0;}")
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "l.c")
+        exe = os.path.join(d, "l")
+        open(c, "w").write("\n".join(lines))
+        subprocess.run(["gcc", "-std=c99", c, "-o", exe], check=True)
+        return subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+
+
+def test_struct_layouts_match_header():
+    from paper_0912_4255_gb300 import _lib
+    got = {}
+    for line in _c_layout().splitlines():
+        parts = line.split()
+        got[(parts[0], parts[1])] = int(parts[2])
+    for cname, cls in (("fstat_detector", _lib.Detector), ("fstat_ephem", _lib.Ephem),
+                       ("fstat_plan_desc", _lib.PlanDesc), ("fstat_template", _lib.Template),
+                       ("fstat_tuning", _lib.Tuning)):
+        assert got[(cname, "size")] == ctypes.sizeof(cls)
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
+def test_strerror(lib):
+    for code in range(-7, 1):
+        assert lib.fstat_strerror(code)
+    assert b"unknown" in lib.fstat_strerror(-99)
+
+
+def _desc(**kw):
+    import synth
+    from paper_0912_4255_gb300 import _desc as mk
+    return mk(synth.tiny_plan(**kw))
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(dt=0.0), -1), (dict(sigma2=-1.0), -1), (dict(n_data=1), -1),
+    (dict(n_fft=1000), -2), (dict(n_fft=1 << 25), -2), (dict(interp=7), -1),
+    (dict(interp=1, taps=3), -6), (dict(precision=9), -1), (dict(window=5), -1),
+])
+def test_plan_rejects_bad_descriptors_on_the_host(lib, kw, code):
+    h = ctypes.c_void_p()
+    need = ctypes.c_size_t()
+    d = _desc(**kw)
+    assert lib.fstat_plan(ctypes.byref(h), ctypes.byref(d), ctypes.byref(need)) == code
+    assert not h.value
+
+
+def test_null_arguments(lib):
+    assert lib.fstat_plan(None, None, None) == -1
+    assert lib.fstat_status(None, None) == -1
+    assert lib.fstat_compute(None, None, None, 0, None, 0, None, None) == -1
+    lib.fstat_destroy(None)

@@ -1,0 +1,164 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI.
+
+Tolerance: max_q |2F_gpu - 2F_oracle| / max(2F_oracle, 4) <= 1e-4 for the
+mixed-precision path (FP64 time map and phase at knots, FP32 per sample,
+FP32 FFT) against the same-algorithm FP64 oracle."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import fstat as F
+from oracle import resample as R
+
+from _gpu import (NOGAPS, injected_series, oracle_two_f, r15, run_compute, run_resample,
+                  tie_margin)
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+
+def test_tiny_nearest_neighbour_all_bins():
+    """12 h, dt 0.5 s, FFT 2^17, NN, one injection at +0.7 Hz."""
+    d = synth.tiny_plan()
+    inj = synth.random_injection(synth.SEED_BASE, df=0.7)
+    x, info = injected_series(d, synth.SEED_BASE, [inj])
+    tm = synth.make_templates(inj.alpha, inj.delta, 0.0, 0, d.n_data)
+    assert tie_margin(d, tm[0]) > 1e-6       # the NN decision is unique in FP32 and FP64
+    got, rc = run_compute(d, x, tm)
+    assert rc == 0
+    ref = oracle_two_f(d, x, tm[0])
+    assert r15(got[0], ref) <= TOL
+    q = int(np.argmax(got[0]))
+    assert abs(F.bin_frequencies(d.n_fft, d.dt)[q] - 0.7) < 2.0 / (d.n_fft * d.dt)
+
+
+@pytest.mark.parametrize("interp", [R.NEAREST, R.SINC])
+def test_resample_stage_matches_oracle_series(interp):
+    """Steps 1-5: w_a, w_b sample by sample and A, B, C, D."""
+    d = synth.PlanDesc(dt=0.5, n_data=40000, n_fft=1 << 16, interp=interp, f_het=150.0,
+                       max_templates=3)
+    gaps = np.array([[3000, 5000], [20000, 20007], [30000, 33000]], np.int64)
+    x, _ = injected_series(d, 7, [synth.random_injection(8, df=0.2)], gaps)
+    tm = synth.make_templates([0.3, 2.5, 4.0], [-0.2, 0.9, 0.1], [0.0, -1e-9, -5e-9],
+                              [0, 100, 1000], [40000, 39000, 30000], 0, 3)
+    (wa, wb, abcd), rc = run_resample(d, x, tm, gaps)
+    assert rc == 0
+    for i in range(3):
+        if interp == R.NEAREST:
+            assert tie_margin(d, tm[i]) > 1e-6
+        r = F.resampled_series(x.astype(np.complex128), tm[i], gaps, d)
+        nb = r["n_b"]
+        scale = np.max(np.abs(r["wa"])) + np.max(np.abs(r["wb"]))
+        assert np.max(np.abs(wa[i, :nb] - r["wa"])) < 2e-5 * scale
+        assert np.max(np.abs(wb[i, :nb] - r["wb"])) < 2e-5 * scale
+        assert np.all(wa[i, nb:] == 0) and np.all(wb[i, nb:] == 0)
+        A, B, C = r["A"], r["B"], r["C"]
+        np.testing.assert_allclose(abcd[i, :3], [A, B, C], rtol=1e-6, atol=1e-6 * (A + B))
+        np.testing.assert_allclose(abcd[i, 3], A * B - C * C, rtol=1e-5)
+
+
+def test_sinc_with_gaps_several_templates():
+    """3 d of data, FFT 2^19, 8-tap Lanczos sinc, gaps, uneven spans and
+    spindowns in one batched launch."""
+    d = synth.PlanDesc(dt=0.5, n_data=3 * 172800 // 2 * 2, n_fft=1 << 19, interp=R.SINC,
+                       f_het=300.0, max_templates=6)
+    gaps = synth.gap_intervals(d.n_data, 0.1, 7200, 43200 // 2, seed=31)
+    injs = [synth.random_injection(40 + i, df=0.05 * (i + 1), fdot=-1e-9 * i) for i in range(2)]
+    x, _ = injected_series(d, 41, injs, gaps)
+    al = [injs[0].alpha, injs[1].alpha, 1.0, 2.0, 3.0, 5.5]
+    de = [injs[0].delta, injs[1].delta, 0.5, -1.2, 0.0, 1.4]
+    fd = [injs[0].fdot, injs[1].fdot, -3e-9, 0.0, -1e-8, -2e-10]
+    ss = [0, 0, 5000, 0, 20000, 777]
+    sl = [d.n_data, d.n_data, 200000, 259200, 150001, 250000]
+    tm = synth.make_templates(al, de, fd, ss, sl, 0, len(gaps))
+    got, rc = run_compute(d, x, tm, gaps)
+    assert rc == 0
+    for i in range(len(tm)):
+        ref = oracle_two_f(d, x, tm[i], gaps)
+        assert r15(got[i], ref) <= TOL, i
+
+
+def test_plain_and_fused_agree():
+    import paper_0912_4255_gb300 as fs
+    d = synth.PlanDesc(dt=0.5, n_data=60000, n_fft=1 << 16, interp=R.SINC, f_het=80.0,
+                       max_templates=2)
+    x, _ = injected_series(d, 3, [synth.random_injection(4, df=0.3)])
+    tm = synth.make_templates([1.0, 2.0], [0.3, -0.3], [0.0, -2e-9], 0, d.n_data)
+    a, rc1 = run_compute(d, x, tm, mode=fs.MODE_FUSED)
+    b, rc2 = run_compute(d, x, tm, mode=fs.MODE_PLAIN)
+    assert rc1 == 0 and rc2 == 0
+    assert r15(a, b) < 1e-6
+    for i in range(2):
+        assert r15(b[i], oracle_two_f(d, x, tm[i])) <= TOL
+
+
+def test_fp64_mode_tight():
+    """All-FP64 path: agreement with the FP64 oracle to 1e-6 (the floor is the
+    cubic interpolation of a, b between knots, ~1e-7, and the float32
+    output)."""
+    d = synth.PlanDesc(dt=0.5, n_data=50000, n_fft=1 << 16, interp=R.SINC, f_het=1000.0,
+                       precision=synth.PREC_FP64, max_templates=2)
+    x, _ = injected_series(d, 5, [synth.random_injection(6, df=0.4, fdot=-5e-9)])
+    tm = synth.make_templates([0.5, 4.4], [0.7, -0.1], [-5e-9, 0.0], 0, d.n_data)
+    got, rc = run_compute(d, x, tm)
+    assert rc == 0
+    for i in range(2):
+        assert r15(got[i], oracle_two_f(d, x, tm[i])) <= 1e-6
+
+
+def test_invalid_template_reports_status_and_nan():
+    import paper_0912_4255_gb300 as fs
+    d = synth.PlanDesc(dt=0.5, n_data=20000, n_fft=1 << 15, interp=R.NEAREST, max_templates=3)
+    x = synth.complex_noise(d.n_data, 1.0, 9)
+    tm = synth.make_templates([1.0, 1.0, 1.0], [0.2, 0.2, 0.2], 0.0,
+                              [0, 15000, 0], [20000, 10000, 20000])
+    got, rc = run_compute(d, x, tm)
+    assert rc == fs._lib.FSTAT_ERANGE
+    assert np.all(np.isfinite(got[0])) and np.all(np.isnan(got[1])) and np.all(np.isfinite(got[2]))
+    assert r15(got[2], oracle_two_f(d, x, tm[2])) <= TOL
+
+
+def test_fft_shorter_than_grid_is_range_error():
+    import paper_0912_4255_gb300 as fs
+    d = synth.PlanDesc(dt=0.5, n_data=5000, n_fft=1 << 12, interp=R.NEAREST, max_templates=1)
+    x = synth.complex_noise(d.n_data, 1.0, 10)
+    tm = synth.make_templates(1.0, 0.2, 0.0, 0, 5000)
+    got, rc = run_compute(d, x, tm)
+    assert rc == fs._lib.FSTAT_ERANGE and np.all(np.isnan(got))
+
+
+def test_host_grid_length_matches_oracle():
+    import paper_0912_4255_gb300 as fs
+    from oracle import timemap as TM
+    d = synth.search_plan(max_templates=16)
+    tm = synth.search_templates(4, 4)
+    plan = fs.Plan(d)
+    nb = fs.fstat_template_nb(plan, tm)
+    for i in range(len(tm)):
+        assert nb[i] == TM.grid(tm[i], d)[1]
+
+
+def test_search_size_full_bins():
+    """Search-sized workload (10 d, 1,728,000 samples, FFT 2^22, 10 % gaps,
+    8-tap sinc) in the launch configuration the benchmark times: every bin
+    of two templates (one at an injection) against the oracle."""
+    d = synth.search_plan(max_templates=4)
+    gaps = synth.gap_intervals(d.n_data, 0.10, 7200, 43200, seed=synth.SEED_BASE + 1)
+    a, dl = synth.fibonacci_sky(1024)
+    inj = synth.random_injection(synth.SEED_BASE + 2, df=0.25, fdot=-1e-9 * 3 / 7,
+                                 alpha=float(a[100]), delta=float(dl[100]))
+    x, info = injected_series(d, synth.SEED_BASE + 1, [inj], gaps)
+    tm = synth.make_templates([a[100], a[700], a[3], a[1000]], [dl[100], dl[700], dl[3], dl[1000]],
+                              [inj.fdot, -1e-9, 0.0, -5e-10], 0, d.n_data, 0, len(gaps))
+    got, rc = run_compute(d, x, tm, gaps)
+    assert rc == 0
+    for i in (0, 1):
+        ref = oracle_two_f(d, x, tm[i], gaps)
+        assert r15(got[i], ref) <= TOL, i
+    # the other two: sampled bins against direct sums of the resampled series
+    fr = F.bin_frequencies(d.n_fft, d.dt)
+    rng = synth.rng(5)
+    for i in (2, 3):
+        q = rng.integers(0, d.n_fft, 24)
+        ref = F.single_bin_two_f_many(x.astype(np.complex128), tm[i], gaps, d, fr[q])
+        assert r15(got[i][q], ref) <= TOL, i
