@@ -180,6 +180,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--templates", type=int, default=N_SKY * N_FDOT,
                     help="templates per GPU per step (default: the whole 8192-template grid)")
+    ap.add_argument("--batch", type=int, default=BATCH,
+                    help="templates per fstat_compute call (size of the 2F ring buffer)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -205,6 +207,8 @@ def main():
 
     desc, x_np, tm, gaps_np = workload(rank, world)
     tm = tm[:args.templates]
+    batch = max(1, min(args.batch, len(tm)))
+    desc = desc.replace(max_templates=batch)
     n_t = len(tm)
     n_fft = int(desc.n_fft)
 
@@ -219,11 +223,11 @@ def main():
     gaps = torch.from_numpy(gaps_np.reshape(-1).copy()).to(dev)
     tmpl = fs.pack_templates(tm, device=dev)
     tsize = fs.TEMPLATE_DTYPE.itemsize
-    out = torch.empty(BATCH * n_fft, dtype=torch.float32, device=dev)
+    out = torch.empty(batch * n_fft, dtype=torch.float32, device=dev)
 
     def step(s):
-        for b0 in range(0, n_t, BATCH):
-            nb = min(BATCH, n_t - b0)
+        for b0 in range(0, n_t, batch):
+            nb = min(batch, n_t - b0)
             fs.fstat_compute(plan, x, tmpl[b0 * tsize:(b0 + nb) * tsize], gaps, out, stream=s)
 
     with torch.cuda.stream(stream):
@@ -281,7 +285,7 @@ def main():
     # ---- end to end through the public API: pinned host in, pinned host out
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(fs, plan, desc, x_np, tm, gaps_np, dev, args, world)
+        e2e = run_e2e(fs, plan, desc, x_np, tm, gaps_np, dev, args, world, batch)
 
     line = {
         "metric": "2F values/sec (templates x freq bins) at rel err <= 1e-4",
@@ -308,7 +312,7 @@ def main():
         dist.destroy_process_group()
 
 
-def run_e2e(fs, plan, desc, x_np, tm, gaps_np, dev, args, world):
+def run_e2e(fs, plan, desc, x_np, tm, gaps_np, dev, args, world, batch):
     """Same metric with host buffers: per step the input series, templates and
     gap list go host->device and every 2F value comes back device->host into
     pinned memory (double-buffered, copies overlapped with compute)."""
@@ -322,8 +326,8 @@ def run_e2e(fs, plan, desc, x_np, tm, gaps_np, dev, args, world):
     x_d = torch.empty_like(x_h, device=dev)
     g_d = torch.empty_like(g_h, device=dev)
     t_d = torch.empty_like(t_h, device=dev)
-    outs = [torch.empty(BATCH * n_fft, dtype=torch.float32, device=dev) for _ in range(2)]
-    host = [torch.empty(BATCH * n_fft, dtype=torch.float32).pin_memory() for _ in range(2)]
+    outs = [torch.empty(batch * n_fft, dtype=torch.float32, device=dev) for _ in range(2)]
+    host = [torch.empty(batch * n_fft, dtype=torch.float32).pin_memory() for _ in range(2)]
     cs, xs = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
     done = [torch.cuda.Event() for _ in range(2)]
     copied = [torch.cuda.Event() for _ in range(2)]
@@ -335,8 +339,8 @@ def run_e2e(fs, plan, desc, x_np, tm, gaps_np, dev, args, world):
             x_d.copy_(x_h, non_blocking=True)
             g_d.copy_(g_h, non_blocking=True)
             t_d.copy_(t_h, non_blocking=True)
-            for i, b0 in enumerate(range(0, n_t, BATCH)):
-                nb = min(BATCH, n_t - b0)
+            for i, b0 in enumerate(range(0, n_t, batch)):
+                nb = min(batch, n_t - b0)
                 j = i & 1
                 cs.wait_event(copied[j])
                 fs.fstat_compute(plan, x_d, t_d[b0 * tsize:(b0 + nb) * tsize], g_d, outs[j], stream=cs)
