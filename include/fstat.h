@@ -203,6 +203,29 @@ int fstat_grad(fstat_plan_t p, const float *x_h, const fstat_template *templates
 int fstat_profile(fstat_plan_t p, int enable);
 int fstat_profile_read(fstat_plan_t p, double *ms, int64_t *launches, int n_kinds);
 
+/* Allocation-free variant of fstat_compute (the paper has no counterpart;
+ * this is a deployment convenience).  For callers that must not allocate
+ * device memory themselves: a plugin inside a framework that owns the
+ * device memory pool, or a real-time loop that cannot afford the implicit
+ * synchronisation of cudaMalloc/cudaFree.  It takes the plan descriptor
+ * directly (no plan, no workspace) and computes exactly what fstat_compute
+ * computes, template by template, using only a fixed scratch array of about
+ * 17 MiB that the library reserves in device memory when it is loaded (on
+ * every GPU that loads it, until the process exits).  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ * Limits: n_fft <= 2^20 (else FSTAT_ERANGE); precision MIXED or FP32 (FP64
+ * gives FSTAT_ENOTSUP); taps <= 16.
+ * The first call on a device looks up the array's device address with that
+ * device current, fills its twiddle tables and synchronises the stream; make
+ * that first call before any stream capture.  All calls on a device share
+ * the one array and leave their last contents in it: calls that overlap on
+ * the GPU race and must be serialised by the caller.  Invalid templates get
+ * NaN outputs; there is no status word to read back.  Pointer arguments as
+ * in fstat_compute (device memory). */
+int fstat_compute_noalloc(const fstat_plan_desc *d, const float *x_h, const fstat_template *templates,
+                          int64_t n_t, const int64_t *gaps, int64_t n_gaps_total, float *twoF,
+                          void *stream);
+
 /* Synchronise the stream, return and clear the first device-side error
  * recorded since the last call (FSTAT_OK if none). */
 int fstat_status(fstat_plan_t p, void *stream);

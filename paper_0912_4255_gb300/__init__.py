@@ -21,7 +21,8 @@ from ._lib import (MODE_FUSED, MODE_PERSISTENT, MODE_PLAIN, NEAREST, PREC_FP32, 
                    PREC_MIXED, SINC, TEMPLATE_DTYPE, WIN_LANCZOS, WIN_RECT)
 
 __all__ = [
-    "FstatError", "Plan", "fstat_plan", "fstat_compute", "fstat_resample", "fstat_grad",
+    "FstatError", "Plan", "fstat_plan", "fstat_compute", "fstat_compute_noalloc", "fstat_resample",
+    "fstat_grad",
     "fstat_status", "fstat_destroy", "fstat_strerror", "fstat_template_nb", "pack_templates",
     "fstat_profile", "fstat_profile_read", "KERNEL_KINDS",
     "NEAREST", "SINC", "WIN_RECT", "WIN_LANCZOS", "PREC_MIXED", "PREC_FP64", "PREC_FP32",
@@ -167,6 +168,21 @@ def fstat_compute(plan: Plan, x_h, templates, gaps=None, twoF=None, stream=None)
     g, ng = _gap_args(gaps)
     _check(plan.lib.fstat_compute(plan.handle, _ptr(x_h), _ptr(templates), n_t, g, ng,
                                   _ptr(twoF), _stream(stream)), "fstat_compute")
+    return twoF
+
+
+def fstat_compute_noalloc(desc, x_h, templates, gaps=None, twoF=None, stream=None):
+    """fstat_compute without a plan or workspace: the library uses its own
+    fixed scratch array (n_fft <= 2^20), for callers that cannot allocate
+    device memory.  ``twoF`` should be passed in by such callers."""
+    import torch
+    lib = _lib.load()
+    n_t = _n_templates(templates)
+    if twoF is None:
+        twoF = torch.empty(n_t * int(desc.n_fft), dtype=torch.float32, device=x_h.device)
+    g, ng = _gap_args(gaps)
+    _check(lib.fstat_compute_noalloc(ctypes.byref(_desc(desc)), _ptr(x_h), _ptr(templates), n_t, g, ng,
+                                     _ptr(twoF), _stream(stream)), "fstat_compute_noalloc")
     return twoF
 
 
