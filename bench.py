@@ -41,15 +41,19 @@ KINDS = ("timemap", "resample", "fft_cols", "fft_rows", "grad_fwd", "grad_adj", 
 
 
 def workload(rank: int = 0, world: int = 1):
+    """The search-sized workload; under N ranks the sky grid has N x 1024
+    points and each rank takes its contiguous share of the N x 8192
+    templates (weak scaling)."""
+    from paper_0912_4255_gb300.shard import shard
     desc = synth.search_plan(max_templates=BATCH)
     seed = synth.SEED_BASE + 1
     gaps = synth.gap_intervals(desc.n_data, GAP_FRAC, 7200, 43200, seed=seed)
     x = synth.zero_gaps(synth.complex_noise(desc.n_data, desc.sigma2, seed), gaps)
     a, d = synth.fibonacci_sky(N_SKY * world)
-    a, d = a[rank::world], d[rank::world]
     fd = np.linspace(-1e-9, 0.0, N_FDOT)
-    tm = synth.make_templates(np.repeat(a, N_FDOT), np.repeat(d, N_FDOT), np.tile(fd, N_SKY),
+    tm = synth.make_templates(np.repeat(a, N_FDOT), np.repeat(d, N_FDOT), np.tile(fd, N_SKY * world),
                               0, desc.n_data, 0, len(gaps))
+    tm, _ = shard(tm, rank, world)
     return desc, x, tm, gaps
 
 
@@ -139,6 +143,60 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    """FP32 FMA peak: 152 SMs x 128 FP32 lanes x 2 flop per clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def algorithmic_per_template(desc):
+    """(FLOPs, bytes) of one template in each kernel, counted from the
+    algorithm (not from the implementation):
+    * FFTs: 5 N log2 N per complex transform of length N, two series (F_a, F_b);
+      the first pass does the log2 N1 part, the second the log2 N2 part;
+    * inter-pass twiddle: one complex multiply per element and series (6 flop);
+    * resampling, per grid point: K taps x (4 flop complex MAC + 5 flop
+      weight) + 16 flop (phase rotation, a/b weights, sums A, B, C);
+    * 2F: 12 flop per bin;
+    * time map: 80-byte knot record per 2^log2h grid points (FP64 work);
+    * bytes: x_h read once (8 B/sample) in the first pass, 2F written (4 B/bin)
+      in the second."""
+    n = int(desc.n_fft)
+    L = int(math.log2(n))
+    l1 = min(12, (L + 1) // 2)
+    if L - l1 > 12:
+        l1 = L - 12
+    l2 = L - l1
+    taps = desc.taps if desc.interp == 1 else 1
+    nb = desc.n_data
+    cols = 2 * 5 * n * l1 + 2 * 6 * n + nb * (taps * 9 + 16)
+    rows = 2 * 5 * n * l2 + 12 * n
+    return {"fft_cols": (cols, 8.0 * desc.n_data), "fft_rows": (rows, 4.0 * n),
+            "timemap": (0.0, 80.0 * (n >> 10)),
+            "persistent": (cols + rows, 8.0 * desc.n_data + 4.0 * n)}
+
+
+def ncu_traffic(kernel: str, templates_per_launch: float):
+    """DRAM bytes per launch from the committed ncu summary
+    (profiles/traffic.md), scaled by templates per launch, or None if the
+    kernels changed since that capture (source digest mismatch)."""
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(path):
+        return None
+    try:
+        from paper_0912_4255_gb300 import build as fsbuild
+        digest = fsbuild._sources_digest()
+        txt = open(path).read()
+        if f"digest: {digest}" not in txt:
+            return None
+        for line in txt.splitlines():
+            p = [c.strip() for c in line.strip().strip("|").split("|")]
+            if len(p) >= 3 and p[0] == kernel:
+                return float(p[1]) * templates_per_launch
+    except (OSError, ValueError):
+        return None
+    return None
+
+
 # ---------------------------------------------------------------- CPU oracle
 
 def _oracle_one(args):
@@ -182,6 +240,10 @@ def main():
                     help="templates per GPU per step (default: the whole 8192-template grid)")
     ap.add_argument("--batch", type=int, default=BATCH,
                     help="templates per fstat_compute call (size of the 2F ring buffer)")
+    ap.add_argument("--mode", default="fused", choices=["fused", "persistent", "plain"],
+                    help="library execution mode")
+    ap.add_argument("--chunk", type=int, default=0,
+                    help="templates per internal launch (0: the library's default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -218,6 +280,9 @@ def main():
         cpu = cpu_oracle_rate(desc, x_np, tm, gaps_np)
 
     plan = fs.Plan(desc, device=dev)
+    mode = {"fused": fs.MODE_FUSED, "persistent": fs.MODE_PERSISTENT, "plain": fs.MODE_PLAIN}[args.mode]
+    if args.chunk or mode != fs.MODE_FUSED:
+        plan.set_tuning(mode=mode, chunk=args.chunk)
     stream = torch.cuda.Stream(device=dev)
     x = torch.from_numpy(x_np.astype(np.complex64)).to(dev)
     gaps = torch.from_numpy(gaps_np.reshape(-1).copy()).to(dev)
@@ -267,21 +332,27 @@ def main():
     value = values_per_step / (ms_per_step / 1e3)
 
     # ---- roofline of the dominant kernel
-    peak, peak_kind = measured_peaks()
-    dom = max(("fft_cols", "fft_rows", "timemap"), key=lambda k: prof[k][0])
-    dom_ms, dom_n = prof[dom]
-    per_launch_templates = n_t * args.steps / max(dom_n, 1)
-    alg = {"fft_cols": 8.0 * desc.n_data, "fft_rows": 4.0 * n_fft,
-           "timemap": 80.0 * (n_fft >> 10)}[dom]
-    achieved = alg * per_launch_templates / (dom_ms / max(dom_n, 1) / 1e3) / 1e9
+    peak_gbs, peak_kind = measured_peaks()
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    peak_tf = fp32_peak_tflops(sm_mhz)
+    per_tpl = algorithmic_per_template(desc)
+    kernels = {}
+    for k in ("timemap", "fft_cols", "fft_rows", "persistent"):
+        k_ms, k_n = prof[k]
+        if not k_n:
+            continue
+        tpl_per_launch = n_t * args.steps / k_n
+        t_launch = k_ms / k_n / 1e3
+        flops, nbytes = per_tpl[k]
+        kernels[k] = {"launches": int(k_n), "ms_per_launch": k_ms / k_n,
+                      "templates_per_launch": tpl_per_launch,
+                      "tflops": flops * tpl_per_launch / t_launch / 1e12,
+                      "alg_gbs": nbytes * tpl_per_launch / t_launch / 1e9}
+    dom = max(kernels, key=lambda k: prof[k][0])
+    kd = kernels[dom]
+    traffic = ncu_traffic(dom, kd["templates_per_launch"])
     launches = sum(v[1] for v in prof.values())
     kernel_ms = {k: round(v[0] / args.steps, 3) for k, v in prof.items() if v[1]}
-    traffic = None
-    tf = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tf):
-        with open(tf) as f:
-            traffic = json.load(f).get(dom)
-
     # ---- end to end through the public API: pinned host in, pinned host out
     e2e = None
     if not args.no_e2e:
@@ -295,11 +366,14 @@ def main():
         "data": "synthetic (seeded complex Gaussian noise with gaps; analytic ephemeris)",
         "config": config_dict(desc, n_t, world),
         "kernel_ms_per_step": kernel_ms,
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": kd["tflops"], "peak": peak_tf,
+                     "unit": "TFLOP/s", "frac": kd["tflops"] / peak_tf,
+                     "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock under load)",
                      "traffic": traffic,
-                     "alg_bytes_per_template": alg},
-        "clocks": clocks, "gpu_launches": int(launches),
+                     "hbm": {"alg_gbs": kd["alg_gbs"], "peak": peak_gbs, "frac": kd["alg_gbs"] / peak_gbs,
+                             "peak_source": peak_kind}},
+        "kernels": kernels,
+        "clocks": clocks, "gpu_launches": int(launches), "tuning": plan.tuning(),
     }
     if e2e is not None:
         line["e2e"] = e2e

@@ -203,6 +203,13 @@ int fstat_grad(fstat_plan_t p, const float *x_h, const fstat_template *templates
 int fstat_profile(fstat_plan_t p, int enable);
 int fstat_profile_read(fstat_plan_t p, double *ms, int64_t *launches, int n_kinds);
 
+/* Test hook for the bounded waits of FSTAT_MODE_PERSISTENT: the next
+ * persistent fstat_compute call makes the row blocks of the given template
+ * wait for one column tile more than will ever finish, with a short wait
+ * limit.  The wait runs out, the launch stops, and fstat_status reports
+ * FSTAT_ETIMEOUT; outputs of that call are then incomplete.  One-shot. */
+int fstat_debug_stall(fstat_plan_t p, int64_t template_index);
+
 /* Allocation-free variant of fstat_compute (the paper has no counterpart;
  * this is a deployment convenience).  For callers that must not allocate
  * device memory themselves: a plugin inside a framework that owns the

@@ -24,7 +24,7 @@ __all__ = [
     "FstatError", "Plan", "fstat_plan", "fstat_compute", "fstat_compute_noalloc", "fstat_resample",
     "fstat_grad",
     "fstat_status", "fstat_destroy", "fstat_strerror", "fstat_template_nb", "pack_templates",
-    "fstat_profile", "fstat_profile_read", "KERNEL_KINDS",
+    "fstat_profile", "fstat_profile_read", "KERNEL_KINDS", "GraphRunner", "fstat_debug_stall",
     "NEAREST", "SINC", "WIN_RECT", "WIN_LANCZOS", "PREC_MIXED", "PREC_FP64", "PREC_FP32",
     "MODE_FUSED", "MODE_PLAIN", "MODE_PERSISTENT", "TEMPLATE_DTYPE",
 ]
@@ -229,6 +229,37 @@ def fstat_profile_read(plan: Plan) -> dict:
     ln = (ctypes.c_int64 * n)()
     _check(plan.lib.fstat_profile_read(plan.handle, ms, ln, n), "fstat_profile_read")
     return {k: (ms[i], ln[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+
+def fstat_debug_stall(plan: Plan, template_index: int):
+    """Arm the one-shot bounded-wait test hook of the persistent mode."""
+    _check(plan.lib.fstat_debug_stall(plan.handle, int(template_index)), "fstat_debug_stall")
+
+
+class GraphRunner:
+    """A CUDA graph holding one fstat_compute call on fixed buffers; replay()
+    reruns the whole batch (in persistent mode: the time map and one
+    persistent launch) without host launch overhead.  The inputs are read
+    from the same device tensors on every replay, so refill them in place."""
+
+    def __init__(self, plan: Plan, x_h, templates, gaps=None, twoF=None, warmup: bool = True):
+        import torch
+        self.plan, self.x_h, self.templates, self.gaps = plan, x_h, templates, gaps
+        n_t = _n_templates(templates)
+        self.twoF = twoF if twoF is not None else torch.empty(n_t * int(plan.desc.n_fft),
+                                                              dtype=torch.float32, device=x_h.device)
+        self.stream = torch.cuda.Stream(device=x_h.device)
+        if warmup:   # first calls set kernel attributes outside the capture
+            with torch.cuda.stream(self.stream):
+                fstat_compute(plan, x_h, templates, gaps, self.twoF, stream=self.stream)
+            self.stream.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=self.stream):
+            fstat_compute(plan, x_h, templates, gaps, self.twoF, stream=self.stream)
+
+    def replay(self):
+        self.graph.replay()
+        return self.twoF
 
 
 def fstat_status(plan: Plan, stream=None, raise_error=True) -> int:

@@ -37,6 +37,9 @@ struct fstat_plan_s {
   size_t need;
   // workspace layout
   size_t off_meta, off_knots, off_part, off_cnt, off_z, off_w, off_grad;
+  size_t off_pcnt, off_sched, off_tcnt;   // persistent mode: counters, schedule, work counts
+  int spin_limit;
+  int64_t stall_template;
   int64_t knot_stride, part_stride, z_stride;
   int rec_bytes, cplx_bytes;
   // per-kernel timing and launch counts
@@ -89,6 +92,8 @@ int choose_shape(fstat_plan_s* p) {
   }
   if (p->tune.mode == FSTAT_MODE_PLAIN) ch = 1;
   if (ch > p->d.max_templates) ch = (int)p->d.max_templates;
+  const bool persistent = p->tune.mode == FSTAT_MODE_PERSISTENT;
+  if (persistent) ch = (int)p->d.max_templates;   // the whole batch in one launch
   if (ch < 1) ch = 1;
   p->chunk = ch;
   // workspace layout
@@ -102,10 +107,13 @@ int choose_shape(fstat_plan_s* p) {
   p->off_knots = o; o = align256(o + (size_t)p->rec_bytes * p->knot_stride * ch);
   p->off_part = o; o = align256(o + sizeof(double) * 3 * p->part_stride * ch);
   p->off_cnt = o; o = align256(o + sizeof(int) * 2 * ch);
-  p->off_z = o; o = align256(o + (size_t)zbytes * ch);
+  p->off_z = o; o = align256(o + (size_t)zbytes * (persistent ? persist_slots() : ch));
   p->off_w = o;
   if (p->tune.mode == FSTAT_MODE_PLAIN) o = align256(o + (size_t)zbytes);
-  p->off_grad = o; o = align256(o + sizeof(double) * grad_work_doubles(ch));
+  p->off_grad = o; o = align256(o + sizeof(double) * grad_work_doubles(persistent ? 1 : ch));
+  p->off_pcnt = o; o = align256(o + sizeof(int) * (2 * (size_t)ch + 2));
+  p->off_sched = o; o = align256(o + sizeof(int) * ((size_t)ch + 2));
+  p->off_tcnt = o; o = align256(o + sizeof(int) * 2 * (size_t)ch);
   p->need = o;
   if (p->ws && p->ws_bytes < p->need) { p->ws = nullptr; p->ws_bytes = 0; }
   return FSTAT_OK;
@@ -179,14 +187,17 @@ int build_tables(fstat_plan_s* p) {
   }
   std::vector<float2> hf(n);
   for (size_t i = 0; i < n; ++i) hf[i] = make_float2((float)hd[i].x, (float)hd[i].y);
-  // cos and sin of pi m / H for m = -H .. H (window of the truncated sinc)
-  double wc[64] = {0};
+  // cos and sin of pi m / H for m = -H .. H (window of the truncated sinc):
+  // 64 doubles, then the same 64 values as floats
+  double wc[96] = {0};
   const int taps = p->d.interp == FSTAT_SINC ? p->d.taps : 2;
   const int half = taps / 2;
   for (int m = -half; m <= half; ++m) {
     wc[2 * (m + half)] = cos(M_PI * m / half);
     wc[2 * (m + half) + 1] = sin(M_PI * m / half);
   }
+  float* wcf = reinterpret_cast<float*>(wc + 64);
+  for (int i = 0; i < 64; ++i) wcf[i] = (float)wc[i];
   const size_t bytes_f = align256(n * sizeof(float2));
   const size_t bytes_d = align256(n * sizeof(double2));
   const size_t total = bytes_f + bytes_d + sizeof(wc);
@@ -284,10 +295,13 @@ int fstat_plan(fstat_plan_t* out, const fstat_plan_desc* d, size_t* workspace_by
   pc.lat = d->det.lat_rad; pc.lon = d->det.lon_rad; pc.gamma = d->det.gamma_rad; pc.radius = d->det.radius_m;
   pc.au = d->eph.au_m; pc.year = d->eph.year_s; pc.sid = d->eph.sidereal_day_s;
   pc.obliq = d->eph.obliquity_rad; pc.orb0 = d->eph.orb_phase0; pc.sid0 = d->eph.sid_phase0;
+  derive_constants(pc);
   p->log2n = ilog2(d->n_fft);
   p->rec_bytes = d->precision == FSTAT_PREC_FP64 ? (int)sizeof(KnotD) : (int)sizeof(KnotF);
   p->cplx_bytes = d->precision == FSTAT_PREC_FP64 ? 16 : 8;
   p->tune.mode = FSTAT_MODE_FUSED;
+  p->spin_limit = 1 << 22;        // x ~256 ns sleeps: about a second
+  p->stall_template = -1;
   rc = choose_shape(p);
   if (rc) { delete p; return rc; }
   rc = build_tables(p);
@@ -302,7 +316,9 @@ int fstat_plan(fstat_plan_t* out, const fstat_plan_desc* d, size_t* workspace_by
 int fstat_set_tuning(fstat_plan_t p, const fstat_tuning* t, size_t* workspace_bytes) {
   if (!p || !t) return FSTAT_EINVAL;
   if (t->mode < FSTAT_MODE_FUSED || t->mode > FSTAT_MODE_PERSISTENT) return FSTAT_EINVAL;
-  if (t->mode == FSTAT_MODE_PERSISTENT) return FSTAT_ENOTSUP;
+  if (t->mode == FSTAT_MODE_PERSISTENT &&
+      (p->d.precision == FSTAT_PREC_FP64 || p->d.max_templates > 65535))
+    return FSTAT_ENOTSUP;
   if (t->chunk < 0 || t->cols < 0 || t->rows < 0 || t->log2_n1 < 0 || t->knot_log2 < 0) return FSTAT_EINVAL;
   const fstat_tuning old = p->tune;
   p->tune = *t;
@@ -370,6 +386,27 @@ int fstat_compute(fstat_plan_t p, const float* x_h, const fstat_template* t, int
   if (n_t > 0 && (!twoF || ((uintptr_t)twoF & 3))) return FSTAT_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const float2* x = reinterpret_cast<const float2*>(x_h);
+  if (p->tune.mode == FSTAT_MODE_PERSISTENT && n_t > 0) {
+    // time map of the whole batch, then one persistent launch over all items
+    const int nt = (int)n_t;
+    Chunk c = chunk_at(p, t, nt);
+    int* pcnt = reinterpret_cast<int*>(p->ws + p->off_pcnt);
+    cudaError_t e = cudaMemsetAsync(c.counters, 0, sizeof(int) * nt, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pcnt, 0, sizeof(int) * (2 * (size_t)nt + 2), s);
+    if (e == cudaSuccess)
+      e = timed(p, K_TIMEMAP, s, [&] { return launch_timemap(p->pc, c, p->log2n, p->tune.mode, gaps, n_gaps_total, p->status, 0, s); });
+    const int stall = p->stall_template >= 0 && p->stall_template < n_t ? (int)p->stall_template : -1;
+    const int limit = stall >= 0 ? (1 << 12) : p->spin_limit;
+    p->stall_template = -1;
+    if (e == cudaSuccess)
+      e = timed(p, K_PERSIST, s, [&] {
+        return launch_persist(p->pc, c, x, gaps, p->wcs, &p->twf, twoF, p->status,
+                              reinterpret_cast<float2*>(p->ws + p->off_z), p->z_stride, pcnt,
+                              reinterpret_cast<int*>(p->ws + p->off_sched),
+                              reinterpret_cast<int*>(p->ws + p->off_tcnt), limit, stall, s);
+      });
+    return e == cudaSuccess ? FSTAT_OK : FSTAT_ECUDA;
+  }
   for (int64_t t0 = 0; t0 < n_t; t0 += p->chunk) {
     const int nt = (int)(n_t - t0 < p->chunk ? n_t - t0 : p->chunk);
     Chunk c = chunk_at(p, t + t0, nt);
@@ -427,6 +464,12 @@ int fstat_grad(fstat_plan_t p, const float* x_h, const fstat_template* t, const 
       });
     if (e != cudaSuccess) return FSTAT_ECUDA;
   }
+  return FSTAT_OK;
+}
+
+int fstat_debug_stall(fstat_plan_t p, int64_t template_index) {
+  if (!p || template_index < 0) return FSTAT_EINVAL;
+  p->stall_template = template_index;
   return FSTAT_OK;
 }
 

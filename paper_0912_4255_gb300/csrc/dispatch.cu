@@ -64,6 +64,9 @@ static cudaError_t do_cols(const PlanConst& pc, const Chunk& c, const Shape& sh,
                            int* status, cudaStream_t s) {
   ColsArgs<R> a;
   a.status = status;
+  a.rr = sh.rows;
+  a.log2rr = 0;
+  while ((1 << a.log2rr) < sh.rows) ++a.log2rr;
   a.pc = pc; a.c = c; a.x = x; a.gaps = gaps; a.wcs = wcs;
   a.tw = *reinterpret_cast<const Tw<R>*>(tw);
   a.ti = ti;

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include <type_traits>
@@ -30,6 +31,13 @@ struct PlanConst {
   double au, year, sid, obliq, orb0, sid0;        // ephemeris
   int32_t log2h;                                  // knot spacing (samples)
   int32_t pad_;
+  // derived on the host (FP64): trigonometric constants of the plan
+  double ce, se;                                  // cos, sin of the obliquity
+  double sl, cl, s2l, c2l;                        // latitude
+  double s2g, c2g;                                // arm-bisector angle
+  double auc, rc;                                 // AU/c, R/c (s)
+  double wo, ws;                                  // orbital and sidereal rates (rad/s)
+  double th0;                                     // sidereal angle of the meridian at t = 0
 };
 
 // Per-template state produced by the time-map kernel and completed by the
@@ -138,16 +146,15 @@ __device__ __forceinline__ Sky<R> make_sky(const PlanConst& pc, R alpha, R delta
   if constexpr (std::is_same<R, float>::value) { sincosf(alpha, &sa, &ca); sincosf(delta, &sd, &cd); }
   else { sincos(alpha, &sa, &ca); sincos(delta, &sd, &cd); }
   s.nx = cd * ca; s.ny = cd * sa; s.nz = sd;
-  const R ce = (R)cos(pc.obliq), se = (R)sin(pc.obliq);
-  const R auc = (R)(pc.au / kC);
+  const R auc = (R)pc.auc;
   s.ox = auc * s.nx;                         // coefficient of cos(phi)
-  s.oy = auc * (ce * s.ny + se * s.nz);      // coefficient of sin(phi)
-  const R sl = (R)sin(pc.lat), cl = (R)cos(pc.lat);
-  s.rz = (R)(pc.radius / kC) * sl * sd;
-  s.rxy = (R)(pc.radius / kC) * cl * cd;
+  s.oy = auc * ((R)pc.ce * s.ny + (R)pc.se * s.nz);      // coefficient of sin(phi)
+  const R sl = (R)pc.sl, cl = (R)pc.cl;
+  s.rz = (R)pc.rc * sl * sd;
+  s.rxy = (R)pc.rc * cl * cd;
   s.alpha = alpha;
-  const R s2g = (R)sin(2 * pc.gamma), c2g = (R)cos(2 * pc.gamma);
-  const R c2l = (R)cos(2 * pc.lat), s2l = (R)sin(2 * pc.lat);
+  const R s2g = (R)pc.s2g, c2g = (R)pc.c2g;
+  const R c2l = (R)pc.c2l, s2l = (R)pc.s2l;
   const R c2d = cd * cd - sd * sd, s2d = 2 * sd * cd;
   s.e3 = s2g * (3 - c2l) * (3 - c2d) / 16;
   s.e4 = -c2g * sl * (3 - c2d) / 4;
@@ -166,25 +173,27 @@ __device__ __forceinline__ void rsincos(R x, R* s, R* c) {
   if constexpr (std::is_same<R, float>::value) sincosf(x, s, c); else sincos(x, s, c);
 }
 
-// t_m(t) and dt_m/dt.
+// t_m(t) and dt_m/dt; sH, cH: sin and cos of the hour angle theta(t) - alpha.
 template <typename R>
-__device__ __forceinline__ void roemer(const PlanConst& pc, const Sky<R>& s, R t, R* tm, R* rate) {
-  const R wo = (R)(kTwoPi / pc.year), ws = (R)(kTwoPi / pc.sid);
+__device__ __forceinline__ void roemer(const PlanConst& pc, const Sky<R>& s, R t, R* tm, R* rate,
+                                       R* sH_out = nullptr, R* cH_out = nullptr) {
+  const R wo = (R)pc.wo, ws = (R)pc.ws;
   R sp, cp, st, ct;
   rsincos<R>((R)pc.orb0 + wo * t, &sp, &cp);
   // hour-angle form: n . r_rot = R cos(lat) cos(delta) cos(theta - alpha) + R sin(lat) sin(delta)
-  rsincos<R>((R)(pc.sid0 + pc.lon) + ws * t - s.alpha, &st, &ct);
+  rsincos<R>((R)pc.th0 + ws * t - s.alpha, &st, &ct);
   *tm = s.ox * cp + s.oy * sp + s.rxy * ct + s.rz;
   *rate = wo * (s.oy * cp - s.ox * sp) - ws * s.rxy * st;
+  if (sH_out) { *sH_out = st; *cH_out = ct; }
 }
 
-// a, b and their time derivatives at detector time t.
+// a, b and their time derivatives from the hour angle H = theta - alpha
+// (x = alpha - theta = -H).
 template <typename R>
-__device__ __forceinline__ void beams(const PlanConst& pc, const Sky<R>& s, R t,
-                                      R* a, R* b, R* da, R* db) {
-  const R ws = (R)(kTwoPi / pc.sid);
-  R sx, cx;
-  rsincos<R>(s.alpha - ((R)(pc.sid0 + pc.lon) + ws * t), &sx, &cx);
+__device__ __forceinline__ void beams_h(const PlanConst& pc, const Sky<R>& s, R sH, R cH,
+                                        R* a, R* b, R* da, R* db) {
+  const R ws = (R)pc.ws;
+  const R sx = -sH, cx = cH;
   const R c2x = cx * cx - sx * sx, s2x = 2 * sx * cx;
   *a = s.e0 + s.e1 * cx + s.e2 * sx + s.e3 * c2x + s.e4 * s2x;
   *b = s.f1 * cx + s.f2 * sx + s.f3 * c2x + s.f4 * s2x;
@@ -193,18 +202,34 @@ __device__ __forceinline__ void beams(const PlanConst& pc, const Sky<R>& s, R t,
   *db = -ws * (-s.f1 * sx + s.f2 * cx - 2 * s.f3 * s2x + 2 * s.f4 * c2x);
 }
 
-// Detector time T with T + t_m(T) = tb (Eq. 21), by Newton's method started
-// from tb - t_m(tb); |dt_m/dt| <~ 1e-4 makes two steps exact to rounding.
+// a, b and their time derivatives at detector time t.
 template <typename R>
-__device__ __forceinline__ R inverse_time(const PlanConst& pc, const Sky<R>& s, R tb) {
+__device__ __forceinline__ void beams(const PlanConst& pc, const Sky<R>& s, R t,
+                                      R* a, R* b, R* da, R* db) {
+  R sH, cH;
+  rsincos<R>((R)pc.th0 + (R)pc.ws * t - s.alpha, &sH, &cH);
+  beams_h<R>(pc, s, sH, cH, a, b, da, db);
+}
+
+// Detector time T with T + t_m(T) = tb (Eq. 21), by Newton's method started
+// from tb - t_m(tb); |dt_m/dt| <~ 1e-4 and |d2t_m/dt2| <~ 1e-10 s^-1 make
+// two steps exact to rounding.  Returns t_m(T), its rate and the hour-angle
+// sine/cosine at T (from the last evaluation, corrected to first order).
+template <typename R>
+__device__ __forceinline__ R inverse_time(const PlanConst& pc, const Sky<R>& s, R tb,
+                                          R* tm_out, R* rate_out, R* sH, R* cH) {
   R tm, rate;
   roemer<R>(pc, s, tb, &tm, &rate);
   R T = tb - tm;
+  R dT = 0;
 #pragma unroll
-  for (int it = 0; it < 3; ++it) {
-    roemer<R>(pc, s, T, &tm, &rate);
-    T -= (T + tm - tb) / (1 + rate);
+  for (int it = 0; it < 2; ++it) {
+    roemer<R>(pc, s, T, &tm, &rate, sH, cH);
+    dT = -(T + tm - tb) / (1 + rate);
+    T += dT;
   }
+  *tm_out = tm + rate * dT;
+  *rate_out = rate;
   return T;
 }
 
@@ -212,143 +237,47 @@ __device__ __forceinline__ R inverse_time(const PlanConst& pc, const Sky<R>& s, 
 
 // Read a complex64 sample as R-precision complex.
 template <typename R>
-__device__ __forceinline__ cpx<R> ldx(const float2* __restrict__ x, int64_t j) {
+__device__ __forceinline__ cpx<R> ldx(const float2* __restrict__ x, int j) {
   const float2 v = __ldg(x + j);
   return cmk<cpx<R>, R>((R)v.x, (R)v.y);
 }
 
 // Validity of data sample j for a template: inside its span and outside its
-// gaps.  ``g`` is a cursor into the sorted gap list, advanced monotonically
-// as the queried j increase.
+// gaps.  The cursor g only moves forward: callers query ascending j (the
+// taps of one sample ascend, and every thread visits its samples in
+// ascending order), so a thread walks the sorted gap list once in total.
 struct GapCursor {
   const int64_t* __restrict__ gaps;  // pairs [start, end)
-  int64_t n, g;
-  int64_t lo, hi;
-  __device__ __forceinline__ void seek(int64_t j) {
-    // first gap whose end is > j (binary search)
-    int64_t a = 0, b = n;
-    while (a < b) {
-      const int64_t m = (a + b) >> 1;
-      if (__ldg(gaps + 2 * m + 1) <= j) a = m + 1; else b = m;
-    }
-    g = a;
+  int n, g;
+  int lo, hi;
+  int cs, ce;                        // the current gap [cs, ce), INT_MAX past the last
+  __device__ __forceinline__ void load() {
+    if (g < n) { cs = (int)__ldg(gaps + 2 * g); ce = (int)__ldg(gaps + 2 * g + 1); }
+    else { cs = 0x7fffffff; ce = 0x7fffffff; }
   }
-  __device__ __forceinline__ bool valid(int64_t j) {
+  __device__ __forceinline__ bool valid(int j) {
     if (j < lo || j >= hi) return false;
-    while (g < n && __ldg(gaps + 2 * g + 1) <= j) ++g;
-    return !(g < n && __ldg(gaps + 2 * g) <= j);
+    while (ce <= j) { ++g; load(); }
+    return j < cs;
+  }
+  // true iff every sample of [j0, j1] is valid; advances the cursor to j0
+  __device__ __forceinline__ bool window_valid(int j0, int j1) {
+    if (j0 < lo || j1 >= hi) return false;
+    while (ce <= j0) { ++g; load(); }
+    return j1 < cs;
   }
 };
 
-// Per-sample time map and weights (steps 2-5) at grid point k < N_b of a
-// template: returns the mask and writes wa = m a y, wb = m b y with
-// y = z(T^k) exp(-2 pi i P(k)), and the beam values a, b.
-template <typename R, int INTERP, int TAPS>
-__device__ __forceinline__ bool sample_weights(
-    const PlanConst& pc, const TmplMeta& m, const typename KnotOf<R>::T* __restrict__ kn,
-    int64_t k, const float2* __restrict__ x, const int64_t* __restrict__ gaps,
-    const double* __restrict__ wcs, cpx<R>& wa, cpx<R>& wb, R& a, R& b) {
-  using C = cpx<R>;
-  const int64_t jint = k >> pc.log2h;
-  const R s = (R)(k & ((1 << pc.log2h) - 1));
-  int64_t ibase;   // integer part of u before the deviation
-  R dev;           // u = ibase + dev
-  R ph;            // phase cycles
-  if constexpr (std::is_same<R, float>::value) {
-    const float4* q = reinterpret_cast<const float4*>(kn + jint);
-    const float4 r0 = __ldg(q), r1 = __ldg(q + 1), r2 = __ldg(q + 2), r3 = __ldg(q + 3), r4 = __ldg(q + 4);
-    ibase = (int64_t)__float_as_int(r0.x) + (k & ((1 << pc.log2h) - 1));
-    dev = r0.y + ((r1.x * s + r0.w) * s + r0.z) * s;
-    ph = r1.y + ((r2.x * s + r1.w) * s + r1.z) * s;
-    a = r2.y + ((r3.x * s + r2.w) * s + r2.z) * s;
-    b = r3.y + ((r4.x * s + r3.w) * s + r3.z) * s;
-  } else {
-    const KnotD& q = kn[jint];
-    const double u = q.U + s + ((q.u3 * s + q.u2) * s + q.u1) * s;
-    const double fl = floor(u);
-    ibase = (int64_t)fl;
-    dev = u - fl;
-    ph = q.P + ((q.p3 * s + q.p2) * s + q.p1) * s;
-    a = q.a0 + ((q.a3 * s + q.a2) * s + q.a1) * s;
-    b = q.b0 + ((q.b3 * s + q.b2) * s + q.b1) * s;
-  }
-  GapCursor gc{gaps, m.n_gaps, 0, m.span_lo, m.span_hi};
-  const int64_t jnn = ibase + (int64_t)floor(dev + (R)0.5);
-  C z;
-  if constexpr (INTERP == FSTAT_NEAREST) {
-    gc.seek(jnn);
-    if (!gc.valid(jnn)) { wa = czero<C>(); wb = czero<C>(); return false; }
-    z = ldx<R>(x, jnn);
-  } else {
-    const int taps = TAPS > 0 ? TAPS : pc.taps;
-    const int half = taps >> 1;
-    const R fl = floor(dev);
-    const int64_t n0 = ibase + (int64_t)fl;
-    // offset from the nearest sample, dn = u - jnn in [-1/2, 1/2]; every
-    // weight is formed from sin/cos of pi dn and pi dn / H, so the tap next
-    // to u gets its value without cancellation and the others have |x| >= 1/2
-    const R dn = dev - (R)(jnn - ibase);
-    gc.seek(n0 - half + 1);
-    if (dn == (R)0) {
-      bool ok = false;
-      for (int64_t j = n0 - half + 1; j <= jnn; ++j) ok = gc.valid(j);
-      if (!ok) { wa = czero<C>(); wb = czero<C>(); return false; }
-      z = ldx<R>(x, jnn);
-    } else {
-      // x = u - j = dn + mq with mq = jnn - j; sin(pi x) = (-1)^mq sin(pi dn);
-      // sin(pi x / H) = sin(pi dn/H) cos(pi mq/H) + cos(pi dn/H) sin(pi mq/H)
-      R S, Cd, sh, chh;
-      if constexpr (std::is_same<R, float>::value) {
-        sincospif(dn, &S, &Cd);
-        sincospif(dn / (R)half, &sh, &chh);
-      } else {
-        sincospi(dn, &S, &Cd);
-        sincospi(dn / (R)half, &sh, &chh);
-      }
-      const R inv_pi2 = (R)(1.0 / (3.14159265358979323846 * 3.14159265358979323846));
-      const bool lanczos = pc.window == FSTAT_WIN_LANCZOS;
-      const int qoff = (int)(jnn - n0);          // 0 or 1
-      C acc = czero<C>();
-      bool msk = false;
-#pragma unroll
-      for (int i = 0; i < (TAPS > 0 ? TAPS : 16); ++i) {
-        if (TAPS == 0 && i >= taps) break;
-        const int mq = half - 1 - i + qoff;       // jnn - j
-        const int64_t j = n0 + 1 - half + i;
-        const R xx = dn + (R)mq;
-        R w = S * inv_pi2 / (xx * xx);
-        if (mq & 1) w = -w;
-        if (lanczos) {
-          w *= (R)half * (sh * (R)wcs[2 * (mq + half)] + chh * (R)wcs[2 * (mq + half) + 1]);
-        } else {
-          w *= (R)3.14159265358979323846 * xx;   // plain truncated sinc: sin(pi x)/(pi x)
-        }
-        const bool ok = gc.valid(j);
-        if (j == jnn) msk = ok;
-        if (ok) {
-          const C v = ldx<R>(x, j);
-          acc.x = fma(w, v.x, acc.x);
-          acc.y = fma(w, v.y, acc.y);
-        }
-      }
-      if (!msk) { wa = czero<C>(); wb = czero<C>(); return false; }
-      z = acc;
-    }
-  }
-  // remove exp(2 pi i P): multiply by exp(-2 pi i r), r = P - rint(P)
-  R r = ph - rint(ph);
-  R sp, cp;
-  if constexpr (std::is_same<R, float>::value) sincospif(2.f * r, &sp, &cp); else sincospi(2.0 * r, &sp, &cp);
-  const C e = cmk<C, R>(cp, -sp);
-  const C y = cmul(z, e);
-  wa = cmk<C, R>(a * y.x, a * y.y);
-  wb = cmk<C, R>(b * y.x, b * y.y);
-  return true;
+__device__ __forceinline__ GapCursor make_cursor(const TmplMeta& m, const int64_t* gaps) {
+  GapCursor gc;
+  gc.gaps = gaps + 2 * m.gap_off;
+  gc.n = (int)m.n_gaps;
+  gc.g = 0;
+  gc.lo = (int)m.span_lo;
+  gc.hi = (int)m.span_hi;
+  gc.load();
+  return gc;
 }
-
-// ---------------------------------------------------------------- FFT
-// In-register DFT of RAD points (forward, e^{-2 pi i jk/RAD}) by radix-2
-// decimation in time; twiddles are compile-time constants.
 
 // cos and sin of 2 pi k / 16 for k = 0..15
 __host__ __device__ constexpr double c16(int k) {
@@ -360,6 +289,203 @@ __host__ __device__ constexpr double c16(int k) {
        : k == 14 ? 0.70710678118654752440 : 0.92387953251128675613;
 }
 __host__ __device__ constexpr double s16(int k) { return c16((k + 12) & 15); }  // sin(2 pi k/16) = cos(2 pi (k-4)/16)
+
+// sin and cos of pi x for |x| <= 1/4 by their Taylor series (terms to x^9
+// and x^10; truncation below 2e-9), single precision.
+__device__ __forceinline__ void sincospi_small(float x, float* s, float* c) {
+  const float t = 3.14159265358979f * x;
+  const float t2 = t * t;
+  *s = t * fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, 2.75573192e-6f, -1.98412698e-4f), 8.33333333e-3f),
+                         -1.66666667e-1f), 1.0f);
+  *c = fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, -2.75573192e-7f, 2.48015873e-5f), -1.38888889e-3f),
+                               4.16666667e-2f), -0.5f), 1.0f);
+}
+
+// exp(-2 pi i r) for |r| <= 1/2: quarter turns split off exactly, the rest
+// (|f| <= 1/8) by sincospi_small.
+__device__ __forceinline__ float2 expm2pi(float r) {
+  const float q = rintf(4.0f * r);
+  const float f = fmaf(-0.25f, q, r);
+  float sn, cs;
+  sincospi_small(2.0f * f, &sn, &cs);
+  // exp(-2 pi i f) = (cs, -sn), times (-i)^q
+  const int qi = ((int)q) & 3;
+  float re = cs, im = -sn;
+  if (qi & 1) { const float t = re; re = im; im = -t; }   // times -i
+  if (qi & 2) { re = -re; im = -im; }                      // times -1
+  return make_float2(re, im);
+}
+
+// Window constants cos/sin(pi m / H), m = -H..H: FP64 at wcs[0..63], the
+// same values rounded to FP32 right after them (wcs + 64 doubles).
+template <typename R> __device__ __forceinline__ const R* win_table(const double* wcs);
+template <> __device__ __forceinline__ const double* win_table<double>(const double* wcs) { return wcs; }
+template <> __device__ __forceinline__ const float* win_table<float>(const double* wcs) {
+  return reinterpret_cast<const float*>(wcs + 64);
+}
+
+// Per-sample time map and weights (steps 2-5) at grid point k < N_b of a
+// template: returns the mask and writes wa = m a y, wb = m b y with
+// y = z(T^k) exp(-2 pi i P(k)), and the beam values a, b.
+template <typename R, int INTERP, int TAPS>
+__device__ __forceinline__ bool sample_weights(
+    const PlanConst& pc, const typename KnotOf<R>::T* __restrict__ kn,
+    int k, const float2* __restrict__ x, GapCursor& gc,
+    const double* __restrict__ wcs, cpx<R>& wa, cpx<R>& wb, R& a, R& b) {
+  using C = cpx<R>;
+  const int jint = k >> pc.log2h;
+  const int sk = k & ((1 << pc.log2h) - 1);
+  const R s = (R)sk;
+  int ibase;       // integer part of u before the deviation
+  R dev;           // u = ibase + dev
+  R ph;            // phase cycles
+  if constexpr (std::is_same<R, float>::value) {
+    const float4* q = reinterpret_cast<const float4*>(kn + jint);
+    const float4 r0 = __ldg(q), r1 = __ldg(q + 1), r2 = __ldg(q + 2), r3 = __ldg(q + 3), r4 = __ldg(q + 4);
+    ibase = __float_as_int(r0.x) + sk;
+    dev = r0.y + ((r1.x * s + r0.w) * s + r0.z) * s;
+    ph = r1.y + ((r2.x * s + r1.w) * s + r1.z) * s;
+    a = r2.y + ((r3.x * s + r2.w) * s + r2.z) * s;
+    b = r3.y + ((r4.x * s + r3.w) * s + r3.z) * s;
+  } else {
+    const KnotD& q = kn[jint];
+    const double u = q.U + s + ((q.u3 * s + q.u2) * s + q.u1) * s;
+    const double fl = floor(u);
+    ibase = (int)fl;
+    dev = u - fl;
+    ph = q.P + ((q.p3 * s + q.p2) * s + q.p1) * s;
+    a = q.a0 + ((q.a3 * s + q.a2) * s + q.a1) * s;
+    b = q.b0 + ((q.b3 * s + q.b2) * s + q.b1) * s;
+  }
+  int jnn_off;                        // jnn - ibase
+  if constexpr (std::is_same<R, float>::value) jnn_off = __float2int_rd(dev + 0.5f);
+  else jnn_off = (int)floor(dev + 0.5);
+  const int jnn = ibase + jnn_off;
+  C z;
+  if constexpr (INTERP == FSTAT_NEAREST) {
+    if (!gc.valid(jnn)) { wa = czero<C>(); wb = czero<C>(); return false; }
+    z = ldx<R>(x, jnn);
+  } else {
+    const int taps = TAPS > 0 ? TAPS : pc.taps;
+    const int half = taps >> 1;
+    // offset from the nearest sample, dn = u - jnn in [-1/2, 1/2]; every
+    // weight is formed from sin/cos of pi dn and pi dn / H, so the tap next
+    // to u gets its value without cancellation and the others have |x| >= 1/2
+    const R dn = dev - (R)jnn_off;
+    const int qoff = dn >= (R)0 ? 0 : 1;       // jnn - floor(u)
+    const int n0 = jnn - qoff;                 // floor(u)
+    if (dn == (R)0) {
+      bool ok = false;
+      for (int j = n0 - half + 1; j <= jnn; ++j) ok = gc.valid(j);
+      if (!ok) { wa = czero<C>(); wb = czero<C>(); return false; }
+      z = ldx<R>(x, jnn);
+    } else {
+      // x = u - j = dn + mq with mq = jnn - j; sin(pi x) = (-1)^mq sin(pi dn);
+      // sin(pi x / H) = sin(pi dn/H) cos(pi mq/H) + cos(pi dn/H) sin(pi mq/H)
+      constexpr int NTAP = TAPS > 0 ? TAPS : 16;
+      // the common case: the whole window is valid data; the loads then go
+      // out from one base pointer before any weight arithmetic
+      const int jlo = n0 + 1 - half;
+      const bool full = gc.window_valid(jlo, jlo + taps - 1);
+      C v[NTAP];
+      if (full) {
+        const float2* xb = x + jlo;
+#pragma unroll
+        for (int i = 0; i < NTAP; ++i) {
+          if (TAPS == 0 && i >= taps) break;
+          const float2 t2 = __ldg(xb + i);
+          v[i] = cmk<C, R>((R)t2.x, (R)t2.y);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < NTAP; ++i) {
+          if (TAPS == 0 && i >= taps) break;
+          int j = jlo + i;
+          j = j < gc.lo ? gc.lo : (j >= gc.hi ? gc.hi - 1 : j);
+          v[i] = ldx<R>(x, j);
+        }
+      }
+      R S, Cd, sh, chh;
+      if constexpr (std::is_same<R, float>::value && TAPS == 8) {
+        // one polynomial at pi dn / 4, then two angle doublings
+        sincospi_small(0.25f * dn, &sh, &chh);
+        const float s2 = 2.0f * sh * chh, c2 = fmaf(chh, chh, -sh * sh);
+        S = 2.0f * s2 * c2;
+        Cd = fmaf(c2, c2, -s2 * s2);
+      } else if constexpr (std::is_same<R, float>::value) {
+        sincospif(dn, &S, &Cd);
+        sincospif(dn / (R)half, &sh, &chh);
+      } else {
+        sincospi(dn, &S, &Cd);
+        sincospi(dn / (R)half, &sh, &chh);
+      }
+      const R inv_pi2 = (R)(1.0 / (3.14159265358979323846 * 3.14159265358979323846));
+      const bool lanczos = pc.window == FSTAT_WIN_LANCZOS;
+      const R* wt = win_table<R>(wcs);
+      const R Sp = S * inv_pi2;
+      C acc = czero<C>();
+      bool msk = false;
+#pragma unroll
+      for (int i = 0; i < NTAP; ++i) {
+        if (TAPS == 0 && i >= taps) break;
+        const int mq = half - 1 - i + qoff;       // jnn - j
+        const int j = n0 + 1 - half + i;
+        const R xx = dn + (R)mq;
+        R w;
+        if constexpr (std::is_same<R, float>::value) w = __fdividef(Sp, xx * xx);
+        else w = Sp / (xx * xx);
+        if (mq & 1) w = -w;
+        if (lanczos) {
+          R cm, sm;
+          if constexpr (TAPS == 8) {
+            // cos, sin(pi mq / 4) = cos, sin(2 pi (2 mq) / 16) with mq = 3 - i + qoff:
+            // two compile-time candidates per tap, chosen by qoff
+            constexpr int dummy = 0;
+            (void)dummy;
+            const int m0 = (2 * (3 - i) + 32) & 15, m1 = (2 * (4 - i) + 32) & 15;
+            const R c0 = (R)c16(m0), c1v = (R)c16(m1), s0 = (R)s16(m0), s1v = (R)s16(m1);
+            cm = qoff ? c1v : c0;
+            sm = qoff ? s1v : s0;
+          } else {
+            cm = __ldg(wt + 2 * (mq + half));
+            sm = __ldg(wt + 2 * (mq + half) + 1);
+          }
+          w *= (R)half * (sh * cm + chh * sm);
+        } else {
+          w *= (R)3.14159265358979323846 * xx;   // plain truncated sinc: sin(pi x)/(pi x)
+        }
+        if (!full) {
+          const bool ok = gc.valid(j);
+          if (j == jnn) msk = ok;
+          if (!ok) w = (R)0;
+        }
+        acc.x = fma(w, v[i].x, acc.x);
+        acc.y = fma(w, v[i].y, acc.y);
+      }
+      if (full) msk = true;
+      if (!msk) { wa = czero<C>(); wb = czero<C>(); return false; }
+      z = acc;
+    }
+  }
+  // remove exp(2 pi i P): multiply by exp(-2 pi i r), r = P - rint(P)
+  R r = ph - rint(ph);
+  C e;
+  if constexpr (std::is_same<R, float>::value) {
+    e = expm2pi(r);
+  } else {
+    R sp, cp;
+    sincospi(2.0 * r, &sp, &cp);
+    e = cmk<C, R>(cp, -sp);
+  }
+  const C y = cmul(z, e);
+  wa = cmk<C, R>(a * y.x, a * y.y);
+  wb = cmk<C, R>(b * y.x, b * y.y);
+  return true;
+}
+
+// ---------------------------------------------------------------- FFT
+// In-register DFT of RAD points (forward, e^{-2 pi i jk/RAD}) by radix-2
+// decimation in time; twiddles are compile-time constants.
 
 template <typename T, int RAD, int STRIDE = 1>
 struct Dft {
@@ -397,21 +523,25 @@ struct Dft {
 // padded shared-memory index: one extra element every 16 avoids bank
 // conflicts of the stride-16 writes of the first radix-16 stage
 __device__ __forceinline__ int pidx(int e) { return e + (e >> 4); }
-template <int LOGN> struct FftGeom {
+// Sequence stride in shared memory.  Fills and epilogues interleave C
+// sequences across the lanes of a half-warp (16 lanes of 8-byte accesses);
+// a stride congruent to 16/C mod 16 puts them on distinct banks.
+template <int LOGN, int C> struct FftGeom {
   static constexpr int N = 1 << LOGN;
-  static constexpr int STRIDE = N + (N >> 4) + 1;   // +1: columns start on different banks
+  static constexpr int BASE = N + (N >> 4);
+  static constexpr int WANT = C >= 16 ? 1 : 16 / C;
+  static constexpr int STRIDE = BASE + ((WANT - (BASE & 15)) & 15);
 };
 
 // One Stockham stage of radix 2^RB over COUNT sequences of length 2^LOGN in
 // shared memory (sequence f at buf + f * STRIDE, padded); NS = 2^NSL is the
 // length of the sub-transforms already done.  Every thread handles UPT units
 // of 16 points; all reads happen before the barrier, all writes after it.
-template <typename R, int LOGN, int RB, int NSL, int NT, int COUNT>
+template <typename R, int LOGN, int RB, int NSL, int NT, int COUNT, int STRIDE>
 __device__ __forceinline__ void stockham_stage(cpx<R>* __restrict__ buf, const cpx<R>* __restrict__ tw) {
   using C = cpx<R>;
   constexpr int N = 1 << LOGN;
   constexpr int RAD = 1 << RB;
-  constexpr int STRIDE = FftGeom<LOGN>::STRIDE;
   constexpr int BPU = 16 / RAD;                   // butterflies per 16-point unit
   constexpr int UNITS_PER_SEQ = N / 16;
   constexpr int UNITS = COUNT * UNITS_PER_SEQ;
@@ -464,19 +594,19 @@ __device__ __forceinline__ void stockham_stage(cpx<R>* __restrict__ buf, const c
 }
 
 // Full FFT: radix-16 stages, then one stage of the remaining radix.
-template <typename R, int LOGN, int NSL, int NT, int COUNT>
+template <typename R, int LOGN, int NSL, int NT, int COUNT, int STRIDE>
 __device__ __forceinline__ void fft_stages(cpx<R>* buf, const cpx<R>* tw) {
   if constexpr (NSL < LOGN) {
     constexpr int REM = LOGN - NSL;
     constexpr int RB = REM >= 4 ? 4 : REM;
-    stockham_stage<R, LOGN, RB, NSL, NT, COUNT>(buf, tw);
-    fft_stages<R, LOGN, NSL + RB, NT, COUNT>(buf, tw);
+    stockham_stage<R, LOGN, RB, NSL, NT, COUNT, STRIDE>(buf, tw);
+    fft_stages<R, LOGN, NSL + RB, NT, COUNT, STRIDE>(buf, tw);
   }
 }
 
-template <typename R, int LOGN, int NT, int COUNT>
+template <typename R, int LOGN, int NT, int COUNT, int STRIDE>
 __device__ __forceinline__ void fft_smem(cpx<R>* buf, const cpx<R>* tw) {
-  fft_stages<R, LOGN, 0, NT, COUNT>(buf, tw);
+  fft_stages<R, LOGN, 0, NT, COUNT, STRIDE>(buf, tw);
 }
 
 // exp(-2 pi i m / 2^L) from the two-level tables
@@ -486,29 +616,24 @@ __device__ __forceinline__ cpx<R> twiddle(const Tw<R>& tw, int L, uint32_t m) {
   return cmul(__ldg(tw.th[L] + (m >> kTwLog)), __ldg(tw.tl[L] + (m & (kTwLo - 1))));
 }
 
-// Block-wide sum of three doubles (any block size multiple of 32, <= 1024).
-__device__ __forceinline__ void block_sum3(double& x, double& y, double& z, double* sh /*[3*32]*/) {
+// Block-wide sum of three values (any block size multiple of 32, <= 1024):
+// warp sums in FP32, the sum over warps in FP64 (the result is in thread 0).
+__device__ __forceinline__ void block_sum3(float fx, float fy, float fz, double& x, double& y, double& z,
+                                           double* sh /*[3*32]*/) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    x += __shfl_down_sync(0xffffffffu, x, o);
-    y += __shfl_down_sync(0xffffffffu, y, o);
-    z += __shfl_down_sync(0xffffffffu, z, o);
+    fx += __shfl_down_sync(0xffffffffu, fx, o);
+    fy += __shfl_down_sync(0xffffffffu, fy, o);
+    fz += __shfl_down_sync(0xffffffffu, fz, o);
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   __syncthreads();
-  if (lane == 0) { sh[wid] = x; sh[32 + wid] = y; sh[64 + wid] = z; }
+  if (lane == 0) { sh[wid] = fx; sh[32 + wid] = fy; sh[64 + wid] = fz; }
   __syncthreads();
-  if (wid == 0) {
+  x = y = z = 0.0;
+  if (threadIdx.x == 0) {
     const int nw = (blockDim.x + 31) >> 5;
-    x = lane < nw ? sh[lane] : 0.0;
-    y = lane < nw ? sh[32 + lane] : 0.0;
-    z = lane < nw ? sh[64 + lane] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      x += __shfl_down_sync(0xffffffffu, x, o);
-      y += __shfl_down_sync(0xffffffffu, y, o);
-      z += __shfl_down_sync(0xffffffffu, z, o);
-    }
+    for (int w = 0; w < nw; ++w) { x += sh[w]; y += sh[32 + w]; z += sh[64 + w]; }
   }
 }
 
@@ -585,7 +710,24 @@ cudaError_t launch_grad_pass(const PlanConst& pc, const Chunk& c, const float2* 
                              double* grad, int* status, int pass, cudaStream_t s);
 size_t grad_work_doubles(int nt);
 int cols_per_block(int precision, int l1);
+int persist_slots();
+size_t persist_smem();
+cudaError_t launch_persist(const PlanConst& pc, const Chunk& c, const float2* x, const int64_t* gaps,
+                           const double* wcs, const void* twf, float* out, int* status, float2* zslots,
+                           int64_t z_stride, int* counters, int* sched, int* cnt, int spin_limit,
+                           int stall_template, cudaStream_t s);
 int rows_per_block(int precision, int l2);
+
+// Fill the derived trigonometric constants of a PlanConst (host, FP64).
+inline void derive_constants(PlanConst& pc) {
+  pc.ce = cos(pc.obliq); pc.se = sin(pc.obliq);
+  pc.sl = sin(pc.lat); pc.cl = cos(pc.lat);
+  pc.s2l = sin(2 * pc.lat); pc.c2l = cos(2 * pc.lat);
+  pc.s2g = sin(2 * pc.gamma); pc.c2g = cos(2 * pc.gamma);
+  pc.auc = pc.au / kC; pc.rc = pc.radius / kC;
+  pc.wo = kTwoPi / pc.year; pc.ws = kTwoPi / pc.sid;
+  pc.th0 = pc.sid0 + pc.lon;
+}
 
 // Host copy of the t_b-grid computation (same formulas, FP64) used to size
 // work and by fstat_template_nb.

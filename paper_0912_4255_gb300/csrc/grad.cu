@@ -97,18 +97,18 @@ __device__ __forceinline__ void sinc_d(R y, R sy, R cy, R& s, R& ds) {
 // mask, the phase P (cycles) and a, b at grid point k.
 template <typename R, int TAPS>
 __device__ __forceinline__ bool sample_with_derivative(
-    const PlanConst& pc, const TmplMeta& m, const typename KnotOf<R>::T* __restrict__ kn, int64_t k,
-    const float2* __restrict__ x, const int64_t* __restrict__ gaps, const double* __restrict__ wcs,
+    const PlanConst& pc, const typename KnotOf<R>::T* __restrict__ kn, int k,
+    const float2* __restrict__ x, GapCursor& gc, const double* __restrict__ wcs,
     cpx<R>& z, cpx<R>& dz, R& u_rel, R& ph, R& a, R& b) {
   using C = cpx<R>;
-  const int64_t jint = k >> pc.log2h;
-  const int64_t sk = k & ((1 << pc.log2h) - 1);
+  const int jint = k >> pc.log2h;
+  const int sk = k & ((1 << pc.log2h) - 1);
   const R s = (R)sk;
-  int64_t ibase;
+  int ibase;
   R dev;
   if constexpr (std::is_same<R, float>::value) {
     const KnotF q = kn[jint];
-    ibase = (int64_t)q.I + sk;
+    ibase = q.I + sk;
     dev = q.F + ((q.u3 * s + q.u2) * s + q.u1) * s;
     ph = q.P + ((q.p3 * s + q.p2) * s + q.p1) * s;
     a = q.a0 + ((q.a3 * s + q.a2) * s + q.a1) * s;
@@ -117,7 +117,7 @@ __device__ __forceinline__ bool sample_with_derivative(
     const KnotD& q = kn[jint];
     const double u = q.U + s + ((q.u3 * s + q.u2) * s + q.u1) * s;
     const double fl = floor(u);
-    ibase = (int64_t)fl;
+    ibase = (int)fl;
     dev = u - fl;
     ph = q.P + ((q.p3 * s + q.p2) * s + q.p1) * s;
     a = q.a0 + ((q.a3 * s + q.a2) * s + q.a1) * s;
@@ -125,13 +125,12 @@ __device__ __forceinline__ bool sample_with_derivative(
   }
   const int taps = TAPS > 0 ? TAPS : pc.taps;
   const int half = taps >> 1;
-  const R fl = floor(dev);
-  const int64_t n0 = ibase + (int64_t)fl;
-  const int64_t jnn = ibase + (int64_t)floor(dev + (R)0.5);
-  const R dn = dev - (R)(jnn - ibase);          // u - jnn in [-1/2, 1/2]
+  const int jnn_off = (int)floor(dev + (R)0.5);
+  const int jnn = ibase + jnn_off;
+  const R dn = dev - (R)jnn_off;                // u - jnn in [-1/2, 1/2]
+  const int qoff = dn >= (R)0 ? 0 : 1;
+  const int n0 = jnn - qoff;
   u_rel = (R)jnn + dn;                          // u in samples from t_start
-  GapCursor gc{gaps, m.n_gaps, 0, m.span_lo, m.span_hi};
-  gc.seek(n0 - half + 1);
   R S, Cd, sh, chh;
   if constexpr (std::is_same<R, float>::value) {
     sincospif(dn, &S, &Cd);
@@ -141,20 +140,20 @@ __device__ __forceinline__ bool sample_with_derivative(
     sincospi(dn / (R)half, &sh, &chh);
   }
   const bool lanczos = pc.window == FSTAT_WIN_LANCZOS;
-  const int qoff = (int)(jnn - n0);
   C acc = czero<C>(), dacc = czero<C>();
   bool msk = false;
 #pragma unroll
   for (int i = 0; i < (TAPS > 0 ? TAPS : 16); ++i) {
     if (TAPS == 0 && i >= taps) break;
     const int mq = half - 1 - i + qoff;
-    const int64_t j = n0 + 1 - half + i;
+    const int j = n0 + 1 - half + i;
     const R xx = dn + (R)mq;
     const R sg = (mq & 1) ? (R)-1 : (R)1;
     R k0, k1;
     sinc_d<R>(xx, sg * S, sg * Cd, k0, k1);
     if (lanczos) {
-      const R cm = (R)wcs[2 * (mq + half)], sm = (R)wcs[2 * (mq + half) + 1];
+      const R* wt = win_table<R>(wcs);
+      const R cm = __ldg(wt + 2 * (mq + half)), sm = __ldg(wt + 2 * (mq + half) + 1);
       const R shm = sh * cm + chh * sm, chm = chh * cm - sh * sm;
       R w0, w1;
       sinc_d<R>(xx / (R)half, shm, chm, w0, w1);
@@ -205,11 +204,11 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_fwd(GradArgs<R> g) {
   const R c0f = (R)(c0 - floor(c0));
   const double fdt = df * g.pc.dt;
   R far = 0, fai = 0, fbr = 0, fbi = 0, sa = 0, sb = 0, sc = 0;
-  for (int64_t k = (int64_t)blockIdx.x * kGradThreads + threadIdx.x; k < m.n_b;
-       k += (int64_t)kGradBlocks * kGradThreads) {
+  GapCursor gc = make_cursor(m, g.gaps);
+  for (int k = blockIdx.x * kGradThreads + threadIdx.x; k < (int)m.n_b; k += kGradBlocks * kGradThreads) {
     C wa, wb;
     R aa, bb;
-    if (!sample_weights<R, FSTAT_SINC, TAPS>(g.pc, m, kn, k, g.x, g.gaps + 2 * m.gap_off, g.wcs, wa, wb, aa, bb))
+    if (!sample_weights<R, FSTAT_SINC, TAPS>(g.pc, kn, k, g.x, gc, g.wcs, wa, wb, aa, bb))
       continue;
     const double ck = fdt * (double)k;
     const C e = expm<R>((R)(ck - floor(ck)) + c0f);
@@ -325,11 +324,11 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_adj(GradArgs<R> g) {
   const R rwo = (R)wo, rws = (R)ws, rphi0 = (R)phi0, rhh0 = (R)hh0;
   const R twopi = (R)kTwoPi;
   R ga = 0, gd = 0, gf = 0, gfd = 0;
-  for (int64_t k = (int64_t)blockIdx.x * kGradThreads + threadIdx.x; k < m.n_b;
-       k += (int64_t)kGradBlocks * kGradThreads) {
+  GapCursor gc = make_cursor(m, g.gaps);
+  for (int k = blockIdx.x * kGradThreads + threadIdx.x; k < (int)m.n_b; k += kGradBlocks * kGradThreads) {
     C z, dz;
     R u, ph, a, b;
-    if (!sample_with_derivative<R, TAPS>(pc, m, kn, k, g.x, g.gaps + 2 * m.gap_off, g.wcs, z, dz, u, ph, a, b))
+    if (!sample_with_derivative<R, TAPS>(pc, kn, k, g.x, gc, g.wcs, z, dz, u, ph, a, b))
       continue;
     // geometry at T^k (smooth quantities, single precision is ample)
     const R tt = u * dtr;                         // T^k - t_start

@@ -64,7 +64,8 @@ constexpr int64_t kOffCnt = al256(kOffPart + 3 * kNaParts * (int64_t)sizeof(doub
 constexpr int64_t kOffStatus = al256(kOffCnt + 2 * (int64_t)sizeof(int));
 constexpr int64_t kOffTw = al256(kOffStatus + (int64_t)sizeof(int));
 constexpr int64_t kOffWcs = al256(kOffTw + tw_entries() * (int64_t)sizeof(float2));
-constexpr int64_t kScratchBytes = al256(kOffWcs + kNaMaxHalf * 2 * (2 * kNaMaxHalf + 1) * (int64_t)sizeof(double));
+constexpr int kWinRow = 96;        // doubles per H: 64 FP64 values, then 64 FP32 copies
+constexpr int64_t kScratchBytes = al256(kOffWcs + kNaMaxHalf * kWinRow * (int64_t)sizeof(double));
 
 // The scratch memory of this entry point (about 17 MiB).
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -101,11 +102,14 @@ __global__ void k_fill_tables(float2* tw, double* wcs) {
     const int m = (int)(i % (2 * kNaMaxHalf + 1)) - kNaMaxHalf;
     double s, c;
     sincospi((double)m / (double)H, &s, &c);
-    // row H-1 holds m = -H..H at positions 0..2H
+    // row H-1 holds m = -H..H at positions 0..2H, and FP32 copies after 64 doubles
     if (m >= -H && m <= H) {
-      double* row = wcs + (int64_t)(H - 1) * 2 * (2 * kNaMaxHalf + 1);
+      double* row = wcs + (int64_t)(H - 1) * kWinRow;
       row[2 * (m + H)] = c;
       row[2 * (m + H) + 1] = s;
+      float* rowf = reinterpret_cast<float*>(row + 64);
+      rowf[2 * (m + H)] = (float)c;
+      rowf[2 * (m + H) + 1] = (float)s;
     }
   }
 }
@@ -170,6 +174,7 @@ extern "C" int fstat_compute_noalloc(const fstat_plan_desc* d, const float* x_h,
   pc.obliq = d->eph.obliquity_rad; pc.orb0 = d->eph.orb_phase0; pc.sid0 = d->eph.sid_phase0;
   pc.log2h = fabs(d->f_het * d->dt) <= 100.0 ? 10 : kNaMinLog2h;
   pc.pad_ = 0;
+  derive_constants(pc);
 
   int L = 0;
   while (((int64_t)1 << L) < d->n_fft) ++L;
@@ -202,7 +207,7 @@ extern "C" int fstat_compute_noalloc(const fstat_plan_desc* d, const float* x_h,
     }
   }
   const int half = pc.taps / 2 > 0 ? pc.taps / 2 : 1;
-  const double* wcs = reinterpret_cast<const double*>(base + kOffWcs) + (int64_t)(half - 1) * 2 * (2 * kNaMaxHalf + 1);
+  const double* wcs = reinterpret_cast<const double*>(base + kOffWcs) + (int64_t)(half - 1) * kWinRow;
   int* status = reinterpret_cast<int*>(base + kOffStatus);
   const float2* x = reinterpret_cast<const float2*>(x_h);
 

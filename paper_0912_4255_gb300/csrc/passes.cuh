@@ -7,11 +7,11 @@
 // Pass A (columns): a block owns C consecutive columns k2 of both series
 // (w_a, w_b), produces their samples (resampled on the fly, or loaded),
 // runs the N1-point FFTs over k1 in shared memory, multiplies by
-// W_N^{p1 k2} and stores the block contiguously as Z[tile][p1][c].
-// Pass B (rows): a block owns RR consecutive rows p1, gathers them from Z
-// (RR*C contiguous values per tile), runs the N2-point FFTs over k2 and
-// writes 2F for every (p1, p2) at the ascending-frequency position
-// q = p1 + N1 ((p2 + N2/2) mod N2).
+// W_N^{p1 k2} and stores into Z laid out as Z[p1 / RR][k2][p1 % RR].
+// Pass B (rows): a block owns the RR consecutive rows p1 of one row block,
+// which are one contiguous run of N2 * RR values per series; it runs the
+// N2-point FFTs over k2 and writes 2F for every (p1, p2) at the
+// ascending-frequency position q = p1 + N1 ((p2 + N2/2) mod N2).
 #pragma once
 
 #include "fstat_internal.cuh"
@@ -31,6 +31,7 @@ struct ColsArgs {
   int ti;        // template within the chunk, or -1 for blockIdx.y
   int tiles_max; // grid.x
   int* status;
+  int rr, log2rr; // rows per block of the second pass (layout of Z)
 };
 
 template <typename R>
@@ -44,27 +45,47 @@ struct RowsArgs {
   int log2cols;
 };
 
+// --------------------------------------------------------------- shapes
+
+// Points per block: 8k complex values in FP32 (64 KB of shared memory with
+// both series), 4k in FP64, so that two blocks share an SM; at most 16
+// columns (rows) per block.
+template <typename R> constexpr int points_per_block() { return std::is_same<R, float>::value ? 8192 : 4096; }
+template <typename R> constexpr int cols_for(int L1) {
+  const int c = (points_per_block<R>() / 2) >> L1;
+  return c > 16 ? 16 : (c < 1 ? 1 : c);
+}
+template <typename R> constexpr int threads_for(int logn, int count) {
+  const int units = (count << logn) / 16;
+  return units >= 512 ? 512 : (units < 32 ? 32 : units);
+}
+template <typename R, int LOGN, int COUNT, int C> constexpr size_t smem_for() {
+  return (size_t)COUNT * FftGeom<LOGN, C>::STRIDE * sizeof(cpx<R>);
+}
+
 // --------------------------------------------------------------- pass A
 
+// two blocks per SM when their shared memory allows it
+template <typename R, int LOGN, int C> constexpr int min_blocks() {
+  return smem_for<R, LOGN, 2 * C, C>() <= 110 * 1024 ? 2 : 1;
+}
+
+// One column tile of pass A for template t (all threads of the block).
+// za: this template's intermediate (a plane; the b plane follows at +N).
 template <typename R, int L1, int C, int NT, int SRC, int TAPS>
-__global__ void __launch_bounds__(NT) k_cols(ColsArgs<R> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void cols_tile(const ColsArgs<R>& a, int t, int tile, cpx<R>* __restrict__ buf,
+                                          double* red, cpx<R>* __restrict__ za, int RRr, int lr) {
   using Cx = cpx<R>;
   using Knot = typename KnotOf<R>::T;
-  Cx* buf = reinterpret_cast<Cx*>(smem_raw);
-  __shared__ double red[96];
   constexpr int N1 = 1 << L1;
-  constexpr int STRIDE = FftGeom<L1>::STRIDE;
-  const int t = a.ti >= 0 ? a.ti : (int)blockIdx.y;
+  constexpr int STRIDE = FftGeom<L1, C>::STRIDE;
   const TmplMeta& m = a.c.meta[t];
   const int L = m.log2n;
   const int N2 = 1 << (L - L1);
   const int tiles = N2 / C;
-  if ((int)blockIdx.x >= tiles || m.status != FSTAT_OK) return;
-  const int c0 = blockIdx.x * C;
-  const int64_t n_b = m.n_b;
+  const int c0 = tile * C;
+  const int n_b = (int)m.n_b;
   const Knot* kn = reinterpret_cast<const Knot*>(a.c.knots) + (int64_t)t * a.c.knot_stride;
-  double sA = 0, sB = 0, sC = 0;
   R pA = 0, pB = 0, pC = 0;
   const Cx* wa_in = nullptr;
   const Cx* wb_in = nullptr;
@@ -72,11 +93,12 @@ __global__ void __launch_bounds__(NT) k_cols(ColsArgs<R> a) {
     wa_in = reinterpret_cast<const Cx*>(a.c.wa) + (int64_t)t * a.c.z_stride;
     wb_in = wa_in + ((int64_t)1 << L);
   }
-  const TmplMeta mm = m;
+  GapCursor gc = make_cursor(m, a.gaps);
+#pragma unroll 2
   for (int i = threadIdx.x; i < C * N1; i += NT) {
     const int c = i & (C - 1);
     const int k1 = i / C;
-    const int64_t k = (int64_t)(c0 + c) + (int64_t)k1 * N2;
+    const int k = c0 + c + k1 * N2;
     Cx va = czero<Cx>(), vb = czero<Cx>();
     if (k < n_b) {
       if constexpr (SRC == SRC_LOAD) {
@@ -84,52 +106,69 @@ __global__ void __launch_bounds__(NT) k_cols(ColsArgs<R> a) {
         vb = wb_in[k];
       } else {
         R aa, bb;
-        const bool mk = sample_weights<R, SRC == SRC_NN ? FSTAT_NEAREST : FSTAT_SINC, TAPS>(
-            a.pc, mm, kn, k, a.x, a.gaps + 2 * mm.gap_off, a.wcs, va, vb, aa, bb);
-        if (mk) { pA += aa * aa; pB += bb * bb; pC += aa * bb; }
+        if (sample_weights<R, SRC == SRC_NN ? FSTAT_NEAREST : FSTAT_SINC, TAPS>(a.pc, kn, k, a.x, gc, a.wcs,
+                                                                              va, vb, aa, bb)) {
+          pA += aa * aa; pB += bb * bb; pC += aa * bb;
+        }
       }
     }
     buf[c * STRIDE + pidx(k1)] = va;
     buf[(C + c) * STRIDE + pidx(k1)] = vb;
   }
   if constexpr (SRC != SRC_LOAD) {
-    sA = pA; sB = pB; sC = pC;
-    block_sum3(sA, sB, sC, red);
+    double sA, sB, sC;
+    block_sum3((float)pA, (float)pB, (float)pC, sA, sB, sC, red);
     double* part = a.c.partials + (int64_t)t * a.c.part_stride * 3;
     if (threadIdx.x == 0) {
-      part[3 * blockIdx.x] = sA; part[3 * blockIdx.x + 1] = sB; part[3 * blockIdx.x + 2] = sC;
+      part[3 * tile] = sA; part[3 * tile + 1] = sB; part[3 * tile + 2] = sC;
     }
     finalize_sums(a.c.meta + t, part, tiles, a.c.counters + t, a.pc.sigma2, nullptr, a.status);
   }
   __syncthreads();
-  fft_smem<R, L1, NT, 2 * C>(buf, a.tw.tl[L1]);
-  Cx* za = reinterpret_cast<Cx*>(a.c.za) + (int64_t)t * a.c.z_stride;
+  fft_smem<R, L1, NT, 2 * C, STRIDE>(buf, a.tw.tl[L1]);
   Cx* zb = za + ((int64_t)1 << L);
-  const int64_t base = (int64_t)blockIdx.x * N1 * C;
+  // element (p1, k2) goes to (p1 >> log2rr) * N2 * RR + k2 * RR + (p1 & (RR-1));
+  // lanes run over r, then c, then the row block: RR * C contiguous values
   for (int i = threadIdx.x; i < C * N1; i += NT) {
-    const int c = i & (C - 1);
-    const int p1 = i / C;
-    const Cx w = twiddle<R>(a.tw, L, (uint32_t)p1 * (uint32_t)(c0 + c));
-    za[base + i] = cmul(buf[c * STRIDE + pidx(p1)], w);
-    zb[base + i] = cmul(buf[(C + c) * STRIDE + pidx(p1)], w);
+    const int r = i & (RRr - 1);
+    const int rest = i >> lr;
+    const int c = rest & (C - 1);
+    const int bb = rest / C;
+    const int p1 = (bb << lr) + r;
+    const int k2 = c0 + c;
+    const Cx w = twiddle<R>(a.tw, L, (uint32_t)p1 * (uint32_t)k2);
+    const int64_t dst = ((int64_t)bb * N2 + k2) * RRr + r;
+    za[dst] = cmul(buf[c * STRIDE + pidx(p1)], w);
+    zb[dst] = cmul(buf[(C + c) * STRIDE + pidx(p1)], w);
   }
+}
+
+template <typename R, int L1, int C, int NT, int SRC, int TAPS>
+__global__ void __launch_bounds__(NT, (min_blocks<R, L1, C>())) k_cols(ColsArgs<R> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[96];
+  const int t = a.ti >= 0 ? a.ti : (int)blockIdx.y;
+  const TmplMeta& m = a.c.meta[t];
+  const int tiles = (1 << (m.log2n - L1)) / C;
+  if ((int)blockIdx.x >= tiles || m.status != FSTAT_OK) return;
+  cpx<R>* za = reinterpret_cast<cpx<R>*>(a.c.za) + (int64_t)t * a.c.z_stride;
+  cols_tile<R, L1, C, NT, SRC, TAPS>(a, t, blockIdx.x, reinterpret_cast<cpx<R>*>(smem_raw), red, za, a.rr,
+                                     a.log2rr);
 }
 
 // --------------------------------------------------------------- pass B
 
+// One row block of pass B for template t; za: the template's intermediate.
 template <typename R, int L2, int RR, int NT>
-__global__ void __launch_bounds__(NT) k_rows(RowsArgs<R> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void rows_tile(const RowsArgs<R>& a, int t, int blk, cpx<R>* __restrict__ buf,
+                                          const cpx<R>* __restrict__ zbase) {
   using Cx = cpx<R>;
-  Cx* buf = reinterpret_cast<Cx*>(smem_raw);
   constexpr int N2 = 1 << L2;
-  constexpr int STRIDE = FftGeom<L2>::STRIDE;
-  const int t = a.ti >= 0 ? a.ti : (int)blockIdx.y;
+  constexpr int STRIDE = FftGeom<L2, RR>::STRIDE;
   const TmplMeta& m = a.c.meta[t];
   const int L = m.log2n;
   const int N1 = 1 << (L - L2);
-  if ((int)blockIdx.x * RR >= N1) return;
-  const int r0 = blockIdx.x * RR;
+  const int r0 = blk * RR;
   float* out = a.out + m.out_off;
   if (m.status != FSTAT_OK) {
     for (int i = threadIdx.x; i < RR * N2; i += NT) {
@@ -138,25 +177,43 @@ __global__ void __launch_bounds__(NT) k_rows(RowsArgs<R> a) {
     }
     return;
   }
-  const int Cc = a.cols, lc = a.log2cols;
-  const Cx* za = reinterpret_cast<const Cx*>(a.c.za) + (int64_t)t * a.c.z_stride;
+  // this block's rows are one contiguous run of N2 * RR values per series,
+  // element (k2, r) at k2 * RR + r
+  const Cx* za = zbase + (int64_t)blk * N2 * RR;
   const Cx* zb = za + ((int64_t)1 << L);
-  const int blk = RR * Cc;
-  for (int i = threadIdx.x; i < RR * N2; i += NT) {
-    const int tile = i / blk;
-    const int rem = i - tile * blk;
-    const int r = rem >> lc;
-    const int c = rem & (Cc - 1);
-    const int k2 = tile * Cc + c;
-    const int64_t src = (int64_t)tile * N1 * Cc + (int64_t)r0 * Cc + rem;
-    buf[r * STRIDE + pidx(k2)] = __ldcs(za + src);
-    buf[(RR + r) * STRIDE + pidx(k2)] = __ldcs(zb + src);
+  constexpr int PER = (RR * N2 + NT - 1) / NT;    // elements per thread
+  constexpr int BATCH = PER >= 4 ? 4 : PER;
+#pragma unroll 1
+  for (int i0 = 0; i0 < PER; i0 += BATCH) {
+    Cx va[BATCH], vb[BATCH];
+#pragma unroll
+    for (int q = 0; q < BATCH; ++q) {
+      const int i = threadIdx.x + (i0 + q) * NT;
+      if (i < RR * N2) {
+        va[q] = __ldcs(za + i);
+        vb[q] = __ldcs(zb + i);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < BATCH; ++q) {
+      const int i = threadIdx.x + (i0 + q) * NT;
+      if (i < RR * N2) {
+        const int r = i & (RR - 1), k2 = i / RR;
+        buf[r * STRIDE + pidx(k2)] = va[q];
+        buf[(RR + r) * STRIDE + pidx(k2)] = vb[q];
+      }
+    }
   }
   __syncthreads();
-  fft_smem<R, L2, NT, 2 * RR>(buf, a.tw.tl[L2]);
-  const double D = m.A * m.B - m.C * m.C;
-  const double sc = 1.0 / (a.pc.sigma2 * D);
-  const R ca = (R)(2.0 * m.B * sc), cb = (R)(2.0 * m.A * sc), cc = (R)(-4.0 * m.C * sc);
+  fft_smem<R, L2, NT, 2 * RR, STRIDE>(buf, a.tw.tl[L2]);
+  R ca, cb, cc;
+  if constexpr (std::is_same<R, float>::value) {
+    ca = m.ca; cb = m.cb; cc = m.cc;
+  } else {
+    const double D = m.A * m.B - m.C * m.C;
+    const double sc = 1.0 / (a.pc.sigma2 * D);
+    ca = 2.0 * m.B * sc; cb = 2.0 * m.A * sc; cc = -4.0 * m.C * sc;
+  }
   for (int i = threadIdx.x; i < RR * N2; i += NT) {
     const int r = i & (RR - 1), p2 = i / RR;
     const Cx fa = buf[r * STRIDE + pidx(p2)];
@@ -167,21 +224,14 @@ __global__ void __launch_bounds__(NT) k_rows(RowsArgs<R> a) {
   }
 }
 
-// --------------------------------------------------------------- shapes
-
-// Columns per block for a first-pass FFT of 2^L1 points: about 16k complex
-// values per block in FP32 (8k in FP64), at most 16 columns.
-template <typename R> constexpr int cols_for(int L1) {
-  const int p = std::is_same<R, float>::value ? 8192 : 4096;
-  const int c = p >> L1;
-  return c > 16 ? 16 : (c < 1 ? 1 : c);
-}
-template <typename R> constexpr int threads_for(int logn, int count) {
-  const int units = (count << logn) / 16;
-  return units >= 512 ? 512 : (units < 32 ? 32 : units);
-}
-template <typename R, int LOGN, int COUNT> constexpr size_t smem_for() {
-  return (size_t)COUNT * FftGeom<LOGN>::STRIDE * sizeof(cpx<R>);
+template <typename R, int L2, int RR, int NT>
+__global__ void __launch_bounds__(NT, (min_blocks<R, L2, RR>())) k_rows(RowsArgs<R> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int t = a.ti >= 0 ? a.ti : (int)blockIdx.y;
+  const TmplMeta& m = a.c.meta[t];
+  if ((int)blockIdx.x * RR >= (1 << (m.log2n - L2))) return;
+  const cpx<R>* za = reinterpret_cast<const cpx<R>*>(a.c.za) + (int64_t)t * a.c.z_stride;
+  rows_tile<R, L2, RR, NT>(a, t, blockIdx.x, reinterpret_cast<cpx<R>*>(smem_raw), za);
 }
 
 }  // namespace fs

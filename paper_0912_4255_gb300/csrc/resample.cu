@@ -38,7 +38,8 @@ k_resample(PlanConst pc, Chunk c, int ti, const float2* __restrict__ x, const in
   R pa = 0, pb = 0, pcc = 0;
   if (k < m.n_b) {
     R aa, bb;
-    if (sample_weights<R, INTERP, TAPS>(pc, m, kn, k, x, gaps + 2 * m.gap_off, wcs, va, vb, aa, bb)) {
+    GapCursor gc = make_cursor(m, gaps);
+    if (sample_weights<R, INTERP, TAPS>(pc, kn, (int)k, x, gc, wcs, va, vb, aa, bb)) {
       pa = aa * aa; pb = bb * bb; pcc = aa * bb;
     }
   }
@@ -46,8 +47,8 @@ k_resample(PlanConst pc, Chunk c, int ti, const float2* __restrict__ x, const in
     oa[k].x = va.x; oa[k].y = va.y;
     ob[k].x = vb.x; ob[k].y = vb.y;
   }
-  double sA = pa, sB = pb, sC = pcc;
-  block_sum3(sA, sB, sC, red);
+  double sA, sB, sC;
+  block_sum3((float)pa, (float)pb, (float)pcc, sA, sB, sC, red);
   double* part = c.partials + (int64_t)t * c.part_stride * 3;
   if (threadIdx.x == 0) {
     part[3 * blockIdx.x] = sA; part[3 * blockIdx.x + 1] = sB; part[3 * blockIdx.x + 2] = sC;

@@ -29,9 +29,8 @@ template <typename R>
 __device__ KnotVal<R> knot_value(const PlanConst& pc, const Sky<R>& sky, double tb0, int64_t k, R fdot) {
   KnotVal<R> v;
   const R tb = (R)(tb0 + (double)k * pc.dt);
-  const R T = inverse_time<R>(pc, sky, tb);
-  R tm, rate;
-  roemer<R>(pc, sky, T, &tm, &rate);
+  R tm, rate, sH, cH;
+  const R T = inverse_time<R>(pc, sky, tb, &tm, &rate, &sH, &cH);
   const R dTdk = (R)pc.dt / (1 + rate);
   v.U = (T - (R)pc.t_start) / (R)pc.dt;
   v.dU = 1 / (1 + rate);
@@ -39,7 +38,7 @@ __device__ KnotVal<R> knot_value(const PlanConst& pc, const Sky<R>& sky, double 
   v.P = (R)pc.f_het * tm + (R)0.5 * fdot * taub * taub;
   v.dP = (R)pc.f_het * rate * dTdk + fdot * taub * (R)pc.dt;
   R a, b, da, db;
-  beams<R>(pc, sky, T, &a, &b, &da, &db);
+  beams_h<R>(pc, sky, sH, cH, &a, &b, &da, &db);
   v.a = a; v.b = b; v.da = da * dTdk; v.db = db * dTdk;
   return v;
 }
@@ -143,11 +142,16 @@ k_timemap(PlanConst pc, const fstat_template* __restrict__ tmpl, TmplMeta* __res
     else if (!allow_ragged && l != log2n_plan) st = st ? st : FSTAT_ENOTSUP;
     else log2n = l;
   }
-  const Sky<double> skyd = make_sky<double>(pc, tp.alpha, tp.delta);
-  const double t_s = pc.t_start + (double)tp.span_start * pc.dt;
-  const double t_e = pc.t_start + (double)(tp.span_start + tp.span_len - 1) * pc.dt;
-  const double tb0 = tb_of(pc, skyd, t_s);
-  const double tbe = tb_of(pc, skyd, t_e);
+  // grid start and end: two threads evaluate t_b(t_s) and t_b(t_e)
+  __shared__ double tb_sh[2];
+  if (threadIdx.x < 2) {
+    const Sky<double> skyd = make_sky<double>(pc, tp.alpha, tp.delta);
+    const int64_t i = threadIdx.x == 0 ? tp.span_start : tp.span_start + tp.span_len - 1;
+    tb_sh[threadIdx.x] = tb_of(pc, skyd, pc.t_start + (double)i * pc.dt);
+  }
+  __syncthreads();
+  const double tb0 = tb_sh[0];
+  const double tbe = tb_sh[1];
   int64_t n_b = (int64_t)floor((tbe - tb0) / pc.dt) + 1;
   if (st == FSTAT_OK && n_b > ((int64_t)1 << log2n)) st = FSTAT_ERANGE;
   if (st != FSTAT_OK) n_b = 0;
@@ -187,7 +191,7 @@ k_timemap(PlanConst pc, const fstat_template* __restrict__ tmpl, TmplMeta* __res
     }
   }
   if (st != FSTAT_OK) return;
-  // --- knot values
+  // --- knot values (sky constants computed once per block)
   const int64_t j0 = (int64_t)blockIdx.x * kKnotThreads;
   if (j0 > n_int) return;
   const Sky<RK> sky = make_sky<RK>(pc, (RK)tp.alpha, (RK)tp.delta);
