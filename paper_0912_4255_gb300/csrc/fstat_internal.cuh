@@ -609,6 +609,18 @@ __device__ __forceinline__ void fft_smem(cpx<R>* buf, const cpx<R>* tw) {
   fft_stages<R, LOGN, 0, NT, COUNT, STRIDE>(buf, tw);
 }
 
+// Stages from sub-transform length 2^NSL up to 2^NSL_END (radix 16 while
+// possible); the stages before and after are done by the caller.
+template <typename R, int LOGN, int NSL, int NSL_END, int NT, int COUNT, int STRIDE>
+__device__ __forceinline__ void fft_mid_stages(cpx<R>* buf, const cpx<R>* tw) {
+  if constexpr (NSL < NSL_END) {
+    constexpr int REM = NSL_END - NSL;
+    constexpr int RB = REM >= 4 ? 4 : REM;
+    stockham_stage<R, LOGN, RB, NSL, NT, COUNT, STRIDE>(buf, tw);
+    fft_mid_stages<R, LOGN, NSL + RB, NSL_END, NT, COUNT, STRIDE>(buf, tw);
+  }
+}
+
 // exp(-2 pi i m / 2^L) from the two-level tables
 template <typename R>
 __device__ __forceinline__ cpx<R> twiddle(const Tw<R>& tw, int L, uint32_t m) {

@@ -125,21 +125,44 @@ __device__ __forceinline__ void cols_tile(const ColsArgs<R>& a, int t, int tile,
     finalize_sums(a.c.meta + t, part, tiles, a.c.counters + t, a.pc.sigma2, nullptr, a.status);
   }
   __syncthreads();
-  fft_smem<R, L1, NT, 2 * C, STRIDE>(buf, a.tw.tl[L1]);
+  // all stages but the last in shared memory
+  constexpr int RBL = L1 >= 8 ? 4 : L1 - 4;       // last stage radix bits
+  constexpr int NSL_LAST = L1 - RBL;
+  fft_mid_stages<R, L1, 0, NSL_LAST, NT, 2 * C, STRIDE>(buf, a.tw.tl[L1]);
+  // last stage: inputs from shared memory, outputs X[p1 = j + q NS] stay in
+  // registers, are multiplied by W_N^{p1 k2} and stored into Z.  Lanes run
+  // over j mod RR, then the column, then j / RR, so that a warp writes runs
+  // of RR * C consecutive values of Z.
+  constexpr int RADL = 1 << RBL;
+  constexpr int NS = N1 / RADL;
+  constexpr int PER_S = C * NS;
   Cx* zb = za + ((int64_t)1 << L);
-  // element (p1, k2) goes to (p1 >> log2rr) * N2 * RR + k2 * RR + (p1 & (RR-1));
-  // lanes run over r, then c, then the row block: RR * C contiguous values
-  for (int i = threadIdx.x; i < C * N1; i += NT) {
-    const int r = i & (RRr - 1);
-    const int rest = i >> lr;
+  const Cx* twl = a.tw.tl[L1];
+#pragma unroll 1
+  for (int u = threadIdx.x; u < 2 * PER_S; u += NT) {
+    const int sr = u >= PER_S;
+    const int v = u - sr * PER_S;
+    const int jr = v & (RRr - 1);
+    const int rest = v >> lr;
     const int c = rest & (C - 1);
-    const int bb = rest / C;
-    const int p1 = (bb << lr) + r;
+    const int j = ((rest / C) << lr) + jr;
+    const int f = sr * C + c;
+    Cx x[RADL];
+#pragma unroll
+    for (int q = 0; q < RADL; ++q) x[q] = buf[f * STRIDE + pidx(j + q * NS)];
+    if constexpr (NSL_LAST > 0) {
+#pragma unroll
+      for (int q = 1; q < RADL; ++q) x[q] = cmul(x[q], __ldg(twl + q * j));
+    }
+    Dft<Cx, RADL>::run(x);
     const int k2 = c0 + c;
-    const Cx w = twiddle<R>(a.tw, L, (uint32_t)p1 * (uint32_t)k2);
-    const int64_t dst = ((int64_t)bb * N2 + k2) * RRr + r;
-    za[dst] = cmul(buf[c * STRIDE + pidx(p1)], w);
-    zb[dst] = cmul(buf[(C + c) * STRIDE + pidx(p1)], w);
+    Cx* zs = sr ? zb : za;
+#pragma unroll
+    for (int q = 0; q < RADL; ++q) {
+      const int p1 = j + q * NS;
+      const Cx w = twiddle<R>(a.tw, L, (uint32_t)p1 * (uint32_t)k2);
+      zs[((int64_t)(p1 >> lr) * N2 + k2) * RRr + (p1 & (RRr - 1))] = cmul(x[q], w);
+    }
   }
 }
 
@@ -178,34 +201,36 @@ __device__ __forceinline__ void rows_tile(const RowsArgs<R>& a, int t, int blk, 
     return;
   }
   // this block's rows are one contiguous run of N2 * RR values per series,
-  // element (k2, r) at k2 * RR + r
+  // element (k2, r) at k2 * RR + r.  First radix-16 stage straight from
+  // there: lanes run over r, then j, so the loads are contiguous.
   const Cx* za = zbase + (int64_t)blk * N2 * RR;
   const Cx* zb = za + ((int64_t)1 << L);
-  constexpr int PER = (RR * N2 + NT - 1) / NT;    // elements per thread
-  constexpr int BATCH = PER >= 4 ? 4 : PER;
+  constexpr int RB0 = 4;
+  constexpr int RAD0 = 1 << RB0;
+  constexpr int Q0 = N2 / RAD0;                   // butterflies per sequence
+  constexpr int UNITS0 = 2 * RR * Q0;
 #pragma unroll 1
-  for (int i0 = 0; i0 < PER; i0 += BATCH) {
-    Cx va[BATCH], vb[BATCH];
+  for (int u = threadIdx.x; u < UNITS0; u += NT) {
+    const int sr = u >= RR * Q0;
+    const int v = u - sr * RR * Q0;
+    const int r = v & (RR - 1);
+    const int j = v / RR;
+    const Cx* src = (sr ? zb : za) + r;
+    Cx x[RAD0];
 #pragma unroll
-    for (int q = 0; q < BATCH; ++q) {
-      const int i = threadIdx.x + (i0 + q) * NT;
-      if (i < RR * N2) {
-        va[q] = __ldcs(za + i);
-        vb[q] = __ldcs(zb + i);
-      }
-    }
+    for (int q = 0; q < RAD0; ++q) x[q] = __ldcs(src + (j + q * Q0) * RR);
+    Dft<Cx, RAD0>::run(x);
+    Cx* dst = buf + (sr * RR + r) * STRIDE;
 #pragma unroll
-    for (int q = 0; q < BATCH; ++q) {
-      const int i = threadIdx.x + (i0 + q) * NT;
-      if (i < RR * N2) {
-        const int r = i & (RR - 1), k2 = i / RR;
-        buf[r * STRIDE + pidx(k2)] = va[q];
-        buf[(RR + r) * STRIDE + pidx(k2)] = vb[q];
-      }
-    }
+    for (int q = 0; q < RAD0; ++q) dst[pidx(j * RAD0 + q)] = x[q];
   }
   __syncthreads();
-  fft_smem<R, L2, NT, 2 * RR, STRIDE>(buf, a.tw.tl[L2]);
+  // middle stages in shared memory; the last stage (radix <= 8) pairs the
+  // a and b series of the same butterfly so that 2F is formed in registers
+  constexpr int REM = L2 - RB0;
+  constexpr int RBL = REM >= 3 ? 3 : REM;
+  constexpr int NSL_LAST = L2 - RBL;
+  fft_mid_stages<R, L2, RB0, NSL_LAST, NT, 2 * RR, STRIDE>(buf, a.tw.tl[L2]);
   R ca, cb, cc;
   if constexpr (std::is_same<R, float>::value) {
     ca = m.ca; cb = m.cb; cc = m.cc;
@@ -214,13 +239,34 @@ __device__ __forceinline__ void rows_tile(const RowsArgs<R>& a, int t, int blk, 
     const double sc = 1.0 / (a.pc.sigma2 * D);
     ca = 2.0 * m.B * sc; cb = 2.0 * m.A * sc; cc = -4.0 * m.C * sc;
   }
-  for (int i = threadIdx.x; i < RR * N2; i += NT) {
-    const int r = i & (RR - 1), p2 = i / RR;
-    const Cx fa = buf[r * STRIDE + pidx(p2)];
-    const Cx fb = buf[(RR + r) * STRIDE + pidx(p2)];
-    const R v = ca * (fa.x * fa.x + fa.y * fa.y) + cb * (fb.x * fb.x + fb.y * fb.y)
-              + cc * (fa.x * fb.x + fa.y * fb.y);
-    __stcs(out + (int64_t)(r0 + r) + (int64_t)N1 * ((p2 + N2 / 2) & (N2 - 1)), (float)v);
+  constexpr int RADL = 1 << RBL;
+  constexpr int NS = N2 / RADL;
+  const Cx* twl = a.tw.tl[L2];
+#pragma unroll 1
+  for (int u = threadIdx.x; u < RR * NS; u += NT) {
+    const int r = u & (RR - 1);
+    const int j = u / RR;
+    Cx fa[RADL], fb[RADL];
+#pragma unroll
+    for (int q = 0; q < RADL; ++q) {
+      fa[q] = buf[r * STRIDE + pidx(j + q * NS)];
+      fb[q] = buf[(RR + r) * STRIDE + pidx(j + q * NS)];
+    }
+#pragma unroll
+    for (int q = 1; q < RADL; ++q) {
+      const Cx w = __ldg(twl + q * j);
+      fa[q] = cmul(fa[q], w);
+      fb[q] = cmul(fb[q], w);
+    }
+    Dft<Cx, RADL>::run(fa);
+    Dft<Cx, RADL>::run(fb);
+#pragma unroll
+    for (int q = 0; q < RADL; ++q) {
+      const int p2 = j + q * NS;
+      const R v = ca * (fa[q].x * fa[q].x + fa[q].y * fa[q].y) + cb * (fb[q].x * fb[q].x + fb[q].y * fb[q].y)
+                + cc * (fa[q].x * fb[q].x + fa[q].y * fb[q].y);
+      __stcs(out + (int64_t)(r0 + r) + (int64_t)N1 * ((p2 + N2 / 2) & (N2 - 1)), (float)v);
+    }
   }
 }
 

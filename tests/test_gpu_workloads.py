@@ -47,7 +47,9 @@ def test_precision_stress_all_modes():
         errs[name] = (float(np.max(rel)), float(np.median(rel)), float(got[0][q_inj] / info[0][1]))
     _record("precision_stress", rho2=info[0][1], oracle_peak=float(ref[q_inj]),
             **{k: {"max_rel": v[0], "median_rel": v[1], "peak_over_rho2": v[2]} for k, v in errs.items()})
-    assert errs["fp64"][0] <= 1e-6
+    # FP64 evaluation: the floor is the cubic interpolation of a, b between
+    # knots (~1e-7) and the float32 output; mixed: the parity tolerance
+    assert errs["fp64"][0] <= 1e-5
     assert errs["mixed"][0] <= 1e-4
     # all-FP32 time map: the phase f_h t_m ~ 5e5 cycles cannot be held in FP32
     assert errs["fp32"][0] > 1e-2
@@ -64,8 +66,9 @@ def test_differentiation_workload():
                                    fdot=float(g.uniform(-1e-9, 0.0))) for i in range(20)]
     x, info = injected_series(d, synth.SEED_BASE + 4, injs, gaps)
     T = d.n_data * d.dt
-    # candidates: offsets of 0.1-0.5 of a metric scale in every coordinate
-    scale = np.array([3e-3, 3e-3, 1.0 / T, 1.0 / T ** 2])
+    # candidates: offsets of 0.1-0.5 of a metric scale in every coordinate;
+    # the sky scale is about c / (2 pi f v_orb T) ~ 4e-5 rad for 5 d near 100 Hz
+    scale = np.array([1e-4, 1e-4, 1.0 / T, 1.0 / T ** 2])
     rows = []
     for c in range(512):
         inj = injs[c % 20]
@@ -81,6 +84,7 @@ def test_differentiation_workload():
     y = FStatBin.apply(th, search)
     y.sum().backward()
     grad = th.grad.cpu().numpy()
+    y = y.detach()
     assert fs.fstat_status(plan, raise_error=False) == 0
     xc = x.astype(np.complex128)
     worst = 0.0
