@@ -290,6 +290,19 @@ __host__ __device__ constexpr double c16(int k) {
 }
 __host__ __device__ constexpr double s16(int k) { return c16((k + 12) & 15); }  // sin(2 pi k/16) = cos(2 pi (k-4)/16)
 
+// Rounding without conversion instructions: adding and subtracting 1.5 * 2^23
+// rounds a float to the nearest integer (ties to even) exactly for
+// |x| < 2^22, and the integer is the low mantissa bits of the sum.
+__device__ __forceinline__ float round_nearest(float x, int* i) {
+  const float t = __fadd_rn(x, 12582912.0f);
+  *i = __float_as_int(t) - 0x4B400000;
+  return __fsub_rn(t, 12582912.0f);
+}
+// exact float of a small non-negative integer (< 2^23)
+__device__ __forceinline__ float small_int_to_float(int k) {
+  return __fsub_rn(__int_as_float(0x4B000000 | k), 8388608.0f);
+}
+
 // sin and cos of pi x for |x| <= 1/4 by their Taylor series (terms to x^9
 // and x^10; truncation below 2e-9), single precision.
 __device__ __forceinline__ void sincospi_small(float x, float* s, float* c) {
@@ -304,12 +317,13 @@ __device__ __forceinline__ void sincospi_small(float x, float* s, float* c) {
 // exp(-2 pi i r) for |r| <= 1/2: quarter turns split off exactly, the rest
 // (|f| <= 1/8) by sincospi_small.
 __device__ __forceinline__ float2 expm2pi(float r) {
-  const float q = rintf(4.0f * r);
+  int qi;
+  const float q = round_nearest(4.0f * r, &qi);
   const float f = fmaf(-0.25f, q, r);
   float sn, cs;
   sincospi_small(2.0f * f, &sn, &cs);
   // exp(-2 pi i f) = (cs, -sn), times (-i)^q
-  const int qi = ((int)q) & 3;
+  qi &= 3;
   float re = cs, im = -sn;
   if (qi & 1) { const float t = re; re = im; im = -t; }   // times -i
   if (qi & 2) { re = -re; im = -im; }                      // times -1
@@ -335,7 +349,8 @@ __device__ __forceinline__ bool sample_weights(
   using C = cpx<R>;
   const int jint = k >> pc.log2h;
   const int sk = k & ((1 << pc.log2h) - 1);
-  const R s = (R)sk;
+  R s;
+  if constexpr (std::is_same<R, float>::value) s = small_int_to_float(sk); else s = (R)sk;
   int ibase;       // integer part of u before the deviation
   R dev;           // u = ibase + dev
   R ph;            // phase cycles
@@ -357,9 +372,17 @@ __device__ __forceinline__ bool sample_weights(
     a = q.a0 + ((q.a3 * s + q.a2) * s + q.a1) * s;
     b = q.b0 + ((q.b3 * s + q.b2) * s + q.b1) * s;
   }
-  int jnn_off;                        // jnn - ibase
-  if constexpr (std::is_same<R, float>::value) jnn_off = __float2int_rd(dev + 0.5f);
-  else jnn_off = (int)floor(dev + 0.5);
+  int jnn_off;                        // jnn - ibase = floor(dev + 1/2)
+  R jnn_f;
+  if constexpr (std::is_same<R, float>::value) {
+    // floor(dev + 1/2): round to nearest, step down where that rounded up
+    // past dev + 1/2 (dev + 1/2 lies in (-1, 3), far inside the exact range)
+    jnn_f = round_nearest(dev + 0.5f, &jnn_off);
+    if (jnn_f > dev + 0.5f) { jnn_f -= 1.0f; --jnn_off; }
+  } else {
+    jnn_f = floor(dev + 0.5);
+    jnn_off = (int)jnn_f;
+  }
   const int jnn = ibase + jnn_off;
   C z;
   if constexpr (INTERP == FSTAT_NEAREST) {
@@ -371,7 +394,7 @@ __device__ __forceinline__ bool sample_weights(
     // offset from the nearest sample, dn = u - jnn in [-1/2, 1/2]; every
     // weight is formed from sin/cos of pi dn and pi dn / H, so the tap next
     // to u gets its value without cancellation and the others have |x| >= 1/2
-    const R dn = dev - (R)jnn_off;
+    const R dn = dev - jnn_f;
     const int qoff = dn >= (R)0 ? 0 : 1;       // jnn - floor(u)
     const int n0 = jnn - qoff;                 // floor(u)
     if (dn == (R)0) {
@@ -422,7 +445,11 @@ __device__ __forceinline__ bool sample_weights(
       const R inv_pi2 = (R)(1.0 / (3.14159265358979323846 * 3.14159265358979323846));
       const bool lanczos = pc.window == FSTAT_WIN_LANCZOS;
       const R* wt = win_table<R>(wcs);
-      const R Sp = S * inv_pi2;
+      // tap i sits at x = dn + mq with mq = (half - 1 - i) + qoff: dn is added
+      // to an exact small integer (a select between two constants), so the
+      // tap at the nearest sample keeps x = dn exactly;
+      // (-1)^mq = (-1)^(half-1-i) (-1)^qoff: the qoff factor goes into Sp
+      const R Sp = (qoff ? -S : S) * inv_pi2;
       C acc = czero<C>();
       bool msk = false;
 #pragma unroll
@@ -430,18 +457,22 @@ __device__ __forceinline__ bool sample_weights(
         if (TAPS == 0 && i >= taps) break;
         const int mq = half - 1 - i + qoff;       // jnn - j
         const int j = n0 + 1 - half + i;
-        const R xx = dn + (R)mq;
+        R xx;
+        if constexpr (TAPS > 0) xx = dn + (qoff ? (R)(TAPS / 2 - i) : (R)(TAPS / 2 - 1 - i));
+        else xx = dn + (R)mq;
         R w;
         if constexpr (std::is_same<R, float>::value) w = __fdividef(Sp, xx * xx);
         else w = Sp / (xx * xx);
-        if (mq & 1) w = -w;
+        if constexpr (TAPS > 0) {
+          if ((TAPS / 2 - 1 - i) & 1) w = -w;
+        } else {
+          if ((mq & 1) != qoff) w = -w;
+        }
         if (lanczos) {
           R cm, sm;
           if constexpr (TAPS == 8) {
             // cos, sin(pi mq / 4) = cos, sin(2 pi (2 mq) / 16) with mq = 3 - i + qoff:
             // two compile-time candidates per tap, chosen by qoff
-            constexpr int dummy = 0;
-            (void)dummy;
             const int m0 = (2 * (3 - i) + 32) & 15, m1 = (2 * (4 - i) + 32) & 15;
             const R c0 = (R)c16(m0), c1v = (R)c16(m1), s0 = (R)s16(m0), s1v = (R)s16(m1);
             cm = qoff ? c1v : c0;
@@ -459,8 +490,13 @@ __device__ __forceinline__ bool sample_weights(
           if (j == jnn) msk = ok;
           if (!ok) w = (R)0;
         }
-        acc.x = fma(w, v[i].x, acc.x);
-        acc.y = fma(w, v[i].y, acc.y);
+        if constexpr (std::is_same<R, float>::value) {
+          acc.x = fmaf(w, v[i].x, acc.x);
+          acc.y = fmaf(w, v[i].y, acc.y);
+        } else {
+          acc.x = fma(w, v[i].x, acc.x);
+          acc.y = fma(w, v[i].y, acc.y);
+        }
       }
       if (full) msk = true;
       if (!msk) { wa = czero<C>(); wb = czero<C>(); return false; }
@@ -468,11 +504,13 @@ __device__ __forceinline__ bool sample_weights(
     }
   }
   // remove exp(2 pi i P): multiply by exp(-2 pi i r), r = P - rint(P)
-  R r = ph - rint(ph);
   C e;
   if constexpr (std::is_same<R, float>::value) {
+    int dummy;
+    const float r = ph - round_nearest(ph, &dummy);
     e = expm2pi(r);
   } else {
+    const R r = ph - rint(ph);
     R sp, cp;
     sincospi(2.0 * r, &sp, &cp);
     e = cmk<C, R>(cp, -sp);
