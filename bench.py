@@ -148,7 +148,7 @@ def fp32_peak_tflops(sm_mhz: float) -> float:
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def algorithmic_per_template(desc):
+def algorithmic_per_template(desc, fused=True):
     """(FLOPs, bytes) of one template in each kernel, counted from the
     algorithm (not from the implementation):
     * FFTs: 5 N log2 N per complex transform of length N, two series (F_a, F_b);
@@ -158,8 +158,11 @@ def algorithmic_per_template(desc):
       weight) + 16 flop (phase rotation, a/b weights, sums A, B, C);
     * 2F: 12 flop per bin;
     * time map: 80-byte knot record per 2^log2h grid points (FP64 work);
-    * bytes: x_h read once (8 B/sample) in the first pass, 2F written (4 B/bin)
-      in the second."""
+    * bytes: x_h read once (8 B/sample) by the resampling, 2F written (4 B/bin)
+      in the second pass.
+    Unfused (split) execution moves the resampling FLOPs and the x_h read out
+    of the first pass into the resample kernel, and adds the resampled series
+    (two complex64 per grid point below n_b), written once and read once."""
     n = int(desc.n_fft)
     L = int(math.log2(n))
     l1 = min(12, (L + 1) // 2)
@@ -168,11 +171,17 @@ def algorithmic_per_template(desc):
     l2 = L - l1
     taps = desc.taps if desc.interp == 1 else 1
     nb = desc.n_data
-    cols = 2 * 5 * n * l1 + 2 * 6 * n + nb * (taps * 9 + 16)
+    fft_a = 2 * 5 * n * l1 + 2 * 6 * n
+    res = nb * (taps * 9 + 16)
     rows = 2 * 5 * n * l2 + 12 * n
-    return {"fft_cols": (cols, 8.0 * desc.n_data), "fft_rows": (rows, 4.0 * n),
-            "timemap": (0.0, 80.0 * (n >> 10)),
-            "persistent": (cols + rows, 8.0 * desc.n_data + 4.0 * n)}
+    out = {"fft_rows": (rows, 4.0 * n), "timemap": (0.0, 80.0 * (n >> 10)),
+           "persistent": (fft_a + res + rows, 8.0 * desc.n_data + 4.0 * n)}
+    if fused:
+        out["fft_cols"] = (fft_a + res, 8.0 * desc.n_data)
+    else:
+        out["resample"] = (res, 8.0 * desc.n_data + 16.0 * nb)
+        out["fft_cols"] = (fft_a, 16.0 * nb)
+    return out
 
 
 def ncu_traffic(kernel: str, templates_per_launch: float):
@@ -240,7 +249,7 @@ def main():
                     help="templates per GPU per step (default: the whole 8192-template grid)")
     ap.add_argument("--batch", type=int, default=BATCH,
                     help="templates per fstat_compute call (size of the 2F ring buffer)")
-    ap.add_argument("--mode", default="fused", choices=["fused", "persistent", "plain"],
+    ap.add_argument("--mode", default="fused", choices=["fused", "split", "persistent", "plain"],
                     help="library execution mode")
     ap.add_argument("--chunk", type=int, default=0,
                     help="templates per internal launch (0: the library's default)")
@@ -280,7 +289,8 @@ def main():
         cpu = cpu_oracle_rate(desc, x_np, tm, gaps_np)
 
     plan = fs.Plan(desc, device=dev)
-    mode = {"fused": fs.MODE_FUSED, "persistent": fs.MODE_PERSISTENT, "plain": fs.MODE_PLAIN}[args.mode]
+    mode = {"fused": fs.MODE_FUSED, "split": fs.MODE_SPLIT, "persistent": fs.MODE_PERSISTENT,
+            "plain": fs.MODE_PLAIN}[args.mode]
     if args.chunk or mode != fs.MODE_FUSED:
         plan.set_tuning(mode=mode, chunk=args.chunk)
     stream = torch.cuda.Stream(device=dev)
@@ -335,9 +345,9 @@ def main():
     peak_gbs, peak_kind = measured_peaks()
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     peak_tf = fp32_peak_tflops(sm_mhz)
-    per_tpl = algorithmic_per_template(desc)
+    per_tpl = algorithmic_per_template(desc, fused=mode in (fs.MODE_FUSED, fs.MODE_PERSISTENT))
     kernels = {}
-    for k in ("timemap", "fft_cols", "fft_rows", "persistent"):
+    for k in ("timemap", "resample", "fft_cols", "fft_rows", "persistent"):
         k_ms, k_n = prof[k]
         if not k_n:
             continue

@@ -73,8 +73,10 @@ enum {
 /* execution mode (fstat_tuning.mode) */
 enum {
   FSTAT_MODE_FUSED      = 0, /* resample+weight fused into the first FFT pass, batched grids */
-  FSTAT_MODE_PLAIN      = 1, /* one template per launch, unfused stages through HBM          */
-  FSTAT_MODE_PERSISTENT = 2  /* one persistent launch over all (template, tile) work items  */
+  FSTAT_MODE_PLAIN      = 1, /* FSTAT_MODE_SPLIT one template per launch                      */
+  FSTAT_MODE_PERSISTENT = 2, /* one persistent launch over all (template, tile) work items  */
+  FSTAT_MODE_SPLIT      = 3  /* resample+weight over contiguous runs into HBM, in the first
+                                pass's column order, then the two FFT passes, batched grids */
 };
 
 /* Detector site (Eqs. 2-3 and Eq. 4pt2): geodetic latitude, east longitude,

@@ -17,7 +17,7 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (MODE_FUSED, MODE_PERSISTENT, MODE_PLAIN, NEAREST, PREC_FP32, PREC_FP64,
+from ._lib import (MODE_FUSED, MODE_PERSISTENT, MODE_PLAIN, MODE_SPLIT, NEAREST, PREC_FP32, PREC_FP64,
                    PREC_MIXED, SINC, TEMPLATE_DTYPE, WIN_LANCZOS, WIN_RECT)
 
 __all__ = [
@@ -26,7 +26,7 @@ __all__ = [
     "fstat_status", "fstat_destroy", "fstat_strerror", "fstat_template_nb", "pack_templates",
     "fstat_profile", "fstat_profile_read", "KERNEL_KINDS", "GraphRunner", "fstat_debug_stall",
     "NEAREST", "SINC", "WIN_RECT", "WIN_LANCZOS", "PREC_MIXED", "PREC_FP64", "PREC_FP32",
-    "MODE_FUSED", "MODE_PLAIN", "MODE_PERSISTENT", "TEMPLATE_DTYPE",
+    "MODE_FUSED", "MODE_PLAIN", "MODE_PERSISTENT", "MODE_SPLIT", "TEMPLATE_DTYPE",
 ]
 
 

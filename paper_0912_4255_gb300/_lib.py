@@ -19,7 +19,7 @@ FSTAT_ECUDA, FSTAT_ETIMEOUT, FSTAT_ENOTSUP, FSTAT_ENOWS = -4, -5, -6, -7
 NEAREST, SINC = 0, 1
 WIN_RECT, WIN_LANCZOS = 0, 1
 PREC_MIXED, PREC_FP64, PREC_FP32 = 0, 1, 2
-MODE_FUSED, MODE_PLAIN, MODE_PERSISTENT = 0, 1, 2
+MODE_FUSED, MODE_PLAIN, MODE_PERSISTENT, MODE_SPLIT = 0, 1, 2, 3
 
 c_double, c_int64, c_int32, c_void_p = ctypes.c_double, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p
 

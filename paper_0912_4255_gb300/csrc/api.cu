@@ -109,7 +109,7 @@ int choose_shape(fstat_plan_s* p) {
   p->off_cnt = o; o = align256(o + sizeof(int) * 2 * ch);
   p->off_z = o; o = align256(o + (size_t)zbytes * (persistent ? persist_slots() : ch));
   p->off_w = o;
-  if (p->tune.mode == FSTAT_MODE_PLAIN) o = align256(o + (size_t)zbytes);
+  if (p->tune.mode == FSTAT_MODE_PLAIN || p->tune.mode == FSTAT_MODE_SPLIT) o = align256(o + (size_t)zbytes * ch);
   p->off_grad = o; o = align256(o + sizeof(double) * grad_work_doubles(persistent ? 1 : ch));
   p->off_pcnt = o; o = align256(o + sizeof(int) * (2 * (size_t)ch + 2));
   p->off_sched = o; o = align256(o + sizeof(int) * ((size_t)ch + 2));
@@ -315,7 +315,7 @@ int fstat_plan(fstat_plan_t* out, const fstat_plan_desc* d, size_t* workspace_by
 
 int fstat_set_tuning(fstat_plan_t p, const fstat_tuning* t, size_t* workspace_bytes) {
   if (!p || !t) return FSTAT_EINVAL;
-  if (t->mode < FSTAT_MODE_FUSED || t->mode > FSTAT_MODE_PERSISTENT) return FSTAT_EINVAL;
+  if (t->mode < FSTAT_MODE_FUSED || t->mode > FSTAT_MODE_SPLIT) return FSTAT_EINVAL;
   if (t->mode == FSTAT_MODE_PERSISTENT &&
       (p->d.precision == FSTAT_PREC_FP64 || p->d.max_templates > 65535))
     return FSTAT_ENOTSUP;
@@ -414,26 +414,13 @@ int fstat_compute(fstat_plan_t p, const float* x_h, const fstat_template* t, int
     if (e == cudaSuccess)
       e = timed(p, K_TIMEMAP, s, [&] { return launch_timemap(p->pc, c, p->log2n, p->tune.mode, gaps, n_gaps_total, p->status, t0, s); });
     if (e != cudaSuccess) return FSTAT_ECUDA;
-    if (p->tune.mode == FSTAT_MODE_PLAIN) {
-      for (int i = 0; i < nt; ++i) {
-        e = timed(p, K_RESAMPLE, s, [&] {
-          return launch_resample_w(p->pc, c, i, p->log2n, x, gaps, p->wcs, c.wa,
-                                   static_cast<char*>(c.wa) + ((size_t)p->cplx_bytes << p->log2n), 0,
-                                   p->d.precision == FSTAT_PREC_FP64, nullptr, p->status, s);
-        });
-        if (e == cudaSuccess) {
-          Chunk ci = c;
-          ci.z_stride = 0;     // the single plain input buffer
-          e = timed(p, K_COLS, s, [&] { return launch_cols_w(p->pc, ci, p->sh, 0, i, x, gaps, p->wcs, &p->twf, &p->twd, p->status, s); });
-        }
-        if (e == cudaSuccess) e = timed(p, K_ROWS, s, [&] { return launch_rows_w(p->pc, c, p->sh, i, &p->twf, &p->twd, twoF, s); });
-        if (e != cudaSuccess) return FSTAT_ECUDA;
-      }
-    } else {
-      e = timed(p, K_COLS, s, [&] { return launch_cols_w(p->pc, c, p->sh, 1, -1, x, gaps, p->wcs, &p->twf, &p->twd, p->status, s); });
-      if (e == cudaSuccess) e = timed(p, K_ROWS, s, [&] { return launch_rows_w(p->pc, c, p->sh, -1, &p->twf, &p->twd, twoF, s); });
-      if (e != cudaSuccess) return FSTAT_ECUDA;
-    }
+    const int fused = p->tune.mode == FSTAT_MODE_FUSED;
+    if (!fused)
+      e = timed(p, K_RESAMPLE, s, [&] { return launch_resample_t(p->pc, c, p->sh, x, gaps, p->wcs, p->status, s); });
+    if (e == cudaSuccess)
+      e = timed(p, K_COLS, s, [&] { return launch_cols_w(p->pc, c, p->sh, fused, -1, x, gaps, p->wcs, &p->twf, &p->twd, p->status, s); });
+    if (e == cudaSuccess) e = timed(p, K_ROWS, s, [&] { return launch_rows_w(p->pc, c, p->sh, -1, &p->twf, &p->twd, twoF, s); });
+    if (e != cudaSuccess) return FSTAT_ECUDA;
   }
   return FSTAT_OK;
 }

@@ -20,7 +20,7 @@ template <typename R, int L1, int SRC, int TAPS>
 cudaError_t run(const ColsArgs<R>& a, dim3 grid, cudaStream_t s) {
   constexpr int C = cols_for<R>(L1);
   constexpr int NT = threads_for<R>(L1, 2 * C);
-  constexpr size_t SM = smem_for<R, L1, 2 * C, C>();
+  constexpr size_t SM = cols_smem<R, L1, C>();
   auto kern = k_cols<R, L1, C, NT, SRC, TAPS>;
   static int attr_done = 0;
   if (!attr_done) {

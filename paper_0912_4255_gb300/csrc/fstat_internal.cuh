@@ -571,12 +571,48 @@ template <int LOGN, int C> struct FftGeom {
   static constexpr int STRIDE = BASE + ((WANT - (BASE & 15)) & 15);
 };
 
+// Twiddles of the Stockham stages, held in shared memory.  The stage of
+// radix 2^RB after sub-transforms of length NS = 2^NSL multiplies input r of
+// butterfly k (k < NS) by W_{NS 2^RB}^{r k}; its table is laid out [r - 1][k]
+// (r = 1 .. 2^RB - 1), so that lanes with consecutive k read consecutive
+// entries.  The first stage (NS = 1) needs none.
+template <int NSL, int RB> constexpr int stage_tw_count() { return NSL > 0 ? ((1 << RB) - 1) << NSL : 0; }
+// radix of the stage after sub-transforms 2^NSL when the stages run to 2^NSL_END
+template <int NSL, int NSL_END> constexpr int mid_rb() { return NSL_END - NSL >= 4 ? 4 : NSL_END - NSL; }
+template <int NSL, int NSL_END> constexpr int mid_tw_count() {
+  if constexpr (NSL < NSL_END) {
+    constexpr int RB = mid_rb<NSL, NSL_END>();
+    return stage_tw_count<NSL, RB>() + mid_tw_count<NSL + RB, NSL_END>();
+  } else {
+    return 0;
+  }
+}
+
+// Fill the table of one stage from the length-2^LOGN table tw (all threads).
+template <typename R, int LOGN, int NSL, int RB, int NT>
+__device__ __forceinline__ void build_stage_tw(cpx<R>* __restrict__ dst, const cpx<R>* __restrict__ tw) {
+  constexpr int CNT = stage_tw_count<NSL, RB>();
+  for (int e = threadIdx.x; e < CNT; e += NT) {
+    const int r = (e >> NSL) + 1, k = e & ((1 << NSL) - 1);
+    dst[e] = __ldg(tw + ((r * k) << (LOGN - NSL - RB)));
+  }
+}
+template <typename R, int LOGN, int NSL, int NSL_END, int NT>
+__device__ __forceinline__ void build_mid_tw(cpx<R>* __restrict__ dst, const cpx<R>* __restrict__ tw) {
+  if constexpr (NSL < NSL_END) {
+    constexpr int RB = mid_rb<NSL, NSL_END>();
+    build_stage_tw<R, LOGN, NSL, RB, NT>(dst, tw);
+    build_mid_tw<R, LOGN, NSL + RB, NSL_END, NT>(dst + stage_tw_count<NSL, RB>(), tw);
+  }
+}
+
 // One Stockham stage of radix 2^RB over COUNT sequences of length 2^LOGN in
 // shared memory (sequence f at buf + f * STRIDE, padded); NS = 2^NSL is the
-// length of the sub-transforms already done.  Every thread handles UPT units
-// of 16 points; all reads happen before the barrier, all writes after it.
+// length of the sub-transforms already done; tws: this stage's twiddle table.
+// Every thread handles UPT units of 16 points; all reads happen before the
+// barrier, all writes after it.
 template <typename R, int LOGN, int RB, int NSL, int NT, int COUNT, int STRIDE>
-__device__ __forceinline__ void stockham_stage(cpx<R>* __restrict__ buf, const cpx<R>* __restrict__ tw) {
+__device__ __forceinline__ void stockham_stage(cpx<R>* __restrict__ buf, const cpx<R>* __restrict__ tws) {
   using C = cpx<R>;
   constexpr int N = 1 << LOGN;
   constexpr int RAD = 1 << RB;
@@ -601,10 +637,7 @@ __device__ __forceinline__ void stockham_stage(cpx<R>* __restrict__ buf, const c
         for (int r = 0; r < RAD; ++r) v[u][bb * RAD + r] = src[pidx(j + r * (N / RAD))];
         if constexpr (NSL > 0) {
 #pragma unroll
-          for (int r = 1; r < RAD; ++r) {
-            const int mexp = (r * k) << (LOGN - NSL - RB);   // W_{NS RAD}^{r k} = W_N^{r k N/(NS RAD)}
-            v[u][bb * RAD + r] = cmul(v[u][bb * RAD + r], __ldg(tw + mexp));
-          }
+          for (int r = 1; r < RAD; ++r) v[u][bb * RAD + r] = cmul(v[u][bb * RAD + r], tws[((r - 1) << NSL) + k]);
         }
         Dft<C, RAD>::run(&v[u][bb * RAD]);
       }
@@ -631,31 +664,15 @@ __device__ __forceinline__ void stockham_stage(cpx<R>* __restrict__ buf, const c
   __syncthreads();
 }
 
-// Full FFT: radix-16 stages, then one stage of the remaining radix.
-template <typename R, int LOGN, int NSL, int NT, int COUNT, int STRIDE>
-__device__ __forceinline__ void fft_stages(cpx<R>* buf, const cpx<R>* tw) {
-  if constexpr (NSL < LOGN) {
-    constexpr int REM = LOGN - NSL;
-    constexpr int RB = REM >= 4 ? 4 : REM;
-    stockham_stage<R, LOGN, RB, NSL, NT, COUNT, STRIDE>(buf, tw);
-    fft_stages<R, LOGN, NSL + RB, NT, COUNT, STRIDE>(buf, tw);
-  }
-}
-
-template <typename R, int LOGN, int NT, int COUNT, int STRIDE>
-__device__ __forceinline__ void fft_smem(cpx<R>* buf, const cpx<R>* tw) {
-  fft_stages<R, LOGN, 0, NT, COUNT, STRIDE>(buf, tw);
-}
-
 // Stages from sub-transform length 2^NSL up to 2^NSL_END (radix 16 while
-// possible); the stages before and after are done by the caller.
+// possible); the stages before and after are done by the caller.  tws: the
+// tables of these stages, one after the other (build_mid_tw).
 template <typename R, int LOGN, int NSL, int NSL_END, int NT, int COUNT, int STRIDE>
-__device__ __forceinline__ void fft_mid_stages(cpx<R>* buf, const cpx<R>* tw) {
+__device__ __forceinline__ void fft_mid_stages(cpx<R>* buf, const cpx<R>* tws) {
   if constexpr (NSL < NSL_END) {
-    constexpr int REM = NSL_END - NSL;
-    constexpr int RB = REM >= 4 ? 4 : REM;
-    stockham_stage<R, LOGN, RB, NSL, NT, COUNT, STRIDE>(buf, tw);
-    fft_mid_stages<R, LOGN, NSL + RB, NSL_END, NT, COUNT, STRIDE>(buf, tw);
+    constexpr int RB = mid_rb<NSL, NSL_END>();
+    stockham_stage<R, LOGN, RB, NSL, NT, COUNT, STRIDE>(buf, tws);
+    fft_mid_stages<R, LOGN, NSL + RB, NSL_END, NT, COUNT, STRIDE>(buf, tws + stage_tw_count<NSL, RB>());
   }
 }
 
@@ -735,7 +752,7 @@ struct Chunk {
   int* counters;          // [nt]
   void* za;               // FFT intermediate [nt][2][n] complex (a plane, b plane)
   int64_t z_stride;       // complex elements per template (2 n)
-  void* wa;               // plain path inputs [nt][2][n]
+  void* wa;               // unfused path: resampled series [nt][2][n], column-tiled
   int nt;
 };
 
@@ -750,6 +767,8 @@ cudaError_t launch_resample_w(const PlanConst& pc, const Chunk& c, int ti, int l
                               const int64_t* gaps, const double* wcs, void* out_a, void* out_b,
                               int64_t out_stride, int out_double, double* abcd, int* status,
                               cudaStream_t s);
+cudaError_t launch_resample_t(const PlanConst& pc, const Chunk& c, const Shape& sh, const float2* x,
+                              const int64_t* gaps, const double* wcs, int* status, cudaStream_t s);
 cudaError_t launch_cols_w(const PlanConst& pc, const Chunk& c, const Shape& sh, int fused, int ti,
                           const float2* x, const int64_t* gaps, const double* wcs, const void* twf,
                           const void* twd, int* status, cudaStream_t s);

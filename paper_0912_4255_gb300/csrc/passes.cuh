@@ -59,16 +59,43 @@ template <typename R> constexpr int threads_for(int logn, int count) {
   const int units = (count << logn) / 16;
   return units >= 512 ? 512 : (units < 32 ? 32 : units);
 }
-template <typename R, int LOGN, int COUNT, int C> constexpr size_t smem_for() {
-  return (size_t)COUNT * FftGeom<LOGN, C>::STRIDE * sizeof(cpx<R>);
+// Stage plan of pass A: shared-memory stages up to sub-transforms of 2^NSL_LAST,
+// then a last stage of radix 2^RBL in registers.  Its shared memory: both
+// series of C columns, the stage twiddle tables, and the two factors of the
+// inter-pass twiddle W_N^{p1 k2} = W_N^{j k2} W_N^{q NS k2} (p1 = j + q NS)
+// for the block's C columns.
+template <int L1> struct PlanA {
+  static constexpr int RBL = L1 >= 8 ? 4 : L1 - 4;
+  static constexpr int NSL_LAST = L1 - RBL;
+  static constexpr int RADL = 1 << RBL;
+  static constexpr int NS = (1 << L1) / RADL;
+  static constexpr int MID_TW = mid_tw_count<0, NSL_LAST>();
+  static constexpr int LAST_TW = stage_tw_count<NSL_LAST, RBL>();
+};
+// Pass B: a first radix-16 stage from global memory, shared-memory stages,
+// a last stage of radix <= 8 in registers.
+template <int L2> struct PlanB {
+  static constexpr int RB0 = 4;
+  static constexpr int RBL = L2 - RB0 >= 3 ? 3 : L2 - RB0;
+  static constexpr int NSL_LAST = L2 - RBL;
+  static constexpr int RADL = 1 << RBL;
+  static constexpr int NS = (1 << L2) / RADL;
+  static constexpr int MID_TW = mid_tw_count<RB0, NSL_LAST>();
+  static constexpr int LAST_TW = stage_tw_count<NSL_LAST, RBL>();
+};
+template <typename R, int L1, int C> constexpr size_t cols_smem() {
+  using P = PlanA<L1>;
+  return ((size_t)2 * C * FftGeom<L1, C>::STRIDE + P::MID_TW + P::LAST_TW + (size_t)C * (P::NS + P::RADL)) *
+         sizeof(cpx<R>);
 }
+template <typename R, int L2, int RR> constexpr size_t rows_smem() {
+  using P = PlanB<L2>;
+  return ((size_t)2 * RR * FftGeom<L2, RR>::STRIDE + P::MID_TW + P::LAST_TW) * sizeof(cpx<R>);
+}
+// two blocks per SM when their shared memory allows it
+constexpr int blocks_for_smem(size_t bytes) { return bytes <= 110 * 1024 ? 2 : 1; }
 
 // --------------------------------------------------------------- pass A
-
-// two blocks per SM when their shared memory allows it
-template <typename R, int LOGN, int C> constexpr int min_blocks() {
-  return smem_for<R, LOGN, 2 * C, C>() <= 110 * 1024 ? 2 : 1;
-}
 
 // One column tile of pass A for template t (all threads of the block).
 // za: this template's intermediate (a plane; the b plane follows at +N).
@@ -90,8 +117,32 @@ __device__ __forceinline__ void cols_tile(const ColsArgs<R>& a, int t, int tile,
   const Cx* wa_in = nullptr;
   const Cx* wb_in = nullptr;
   if constexpr (SRC == SRC_LOAD) {
-    wa_in = reinterpret_cast<const Cx*>(a.c.wa) + (int64_t)t * a.c.z_stride;
+    // the tiled resampler's order W[k2 / C][k1][k2 % C]: this tile's C * N1
+    // points of each series are contiguous, point i = c + C k1 at offset i
+    wa_in = reinterpret_cast<const Cx*>(a.c.wa) + (int64_t)t * a.c.z_stride + (int64_t)tile * (C * N1);
     wb_in = wa_in + ((int64_t)1 << L);
+  }
+  // twiddle tables (read after the barriers that end the fill)
+  using PA = PlanA<L1>;
+  constexpr int RBL = PA::RBL;
+  constexpr int NSL_LAST = PA::NSL_LAST;
+  constexpr int RADL = PA::RADL;
+  constexpr int NS = PA::NS;
+  cpx<R>* tws = buf + 2 * C * STRIDE;     // shared-memory stages
+  cpx<R>* tlast = tws + PA::MID_TW;       // last stage, [q - 1][j]
+  cpx<R>* ta = tlast + PA::LAST_TW;       // [c][j]: W_N^{j (c0 + c)}, j < NS
+  cpx<R>* tb = ta + C * NS;               // [c][q]: W_N^{q NS (c0 + c)}, q < RADL
+  build_mid_tw<R, L1, 0, NSL_LAST, NT>(tws, a.tw.tl[L1]);
+  build_stage_tw<R, L1, NSL_LAST, RBL, NT>(tlast, a.tw.tl[L1]);
+  for (int e = threadIdx.x; e < C * (NS + RADL); e += NT) {
+    if (e < C * NS) {
+      const int c = e / NS, j = e - c * NS;
+      ta[e] = twiddle<R>(a.tw, L, (uint32_t)j * (uint32_t)(c0 + c));
+    } else {
+      const int e2 = e - C * NS;
+      const int c = e2 / RADL, q = e2 - c * RADL;
+      tb[e2] = twiddle<R>(a.tw, L, (uint32_t)(q * NS) * (uint32_t)(c0 + c));
+    }
   }
   GapCursor gc = make_cursor(m, a.gaps);
 #pragma unroll 2
@@ -102,8 +153,8 @@ __device__ __forceinline__ void cols_tile(const ColsArgs<R>& a, int t, int tile,
     Cx va = czero<Cx>(), vb = czero<Cx>();
     if (k < n_b) {
       if constexpr (SRC == SRC_LOAD) {
-        va = wa_in[k];
-        vb = wb_in[k];
+        va = __ldcs(wa_in + i);
+        vb = __ldcs(wb_in + i);
       } else {
         R aa, bb;
         if (sample_weights<R, SRC == SRC_NN ? FSTAT_NEAREST : FSTAT_SINC, TAPS>(a.pc, kn, k, a.x, gc, a.wcs,
@@ -126,18 +177,13 @@ __device__ __forceinline__ void cols_tile(const ColsArgs<R>& a, int t, int tile,
   }
   __syncthreads();
   // all stages but the last in shared memory
-  constexpr int RBL = L1 >= 8 ? 4 : L1 - 4;       // last stage radix bits
-  constexpr int NSL_LAST = L1 - RBL;
-  fft_mid_stages<R, L1, 0, NSL_LAST, NT, 2 * C, STRIDE>(buf, a.tw.tl[L1]);
+  fft_mid_stages<R, L1, 0, NSL_LAST, NT, 2 * C, STRIDE>(buf, tws);
   // last stage: inputs from shared memory, outputs X[p1 = j + q NS] stay in
   // registers, are multiplied by W_N^{p1 k2} and stored into Z.  Lanes run
   // over j mod RR, then the column, then j / RR, so that a warp writes runs
   // of RR * C consecutive values of Z.
-  constexpr int RADL = 1 << RBL;
-  constexpr int NS = N1 / RADL;
   constexpr int PER_S = C * NS;
   Cx* zb = za + ((int64_t)1 << L);
-  const Cx* twl = a.tw.tl[L1];
 #pragma unroll 1
   for (int u = threadIdx.x; u < 2 * PER_S; u += NT) {
     const int sr = u >= PER_S;
@@ -150,24 +196,23 @@ __device__ __forceinline__ void cols_tile(const ColsArgs<R>& a, int t, int tile,
     Cx x[RADL];
 #pragma unroll
     for (int q = 0; q < RADL; ++q) x[q] = buf[f * STRIDE + pidx(j + q * NS)];
-    if constexpr (NSL_LAST > 0) {
 #pragma unroll
-      for (int q = 1; q < RADL; ++q) x[q] = cmul(x[q], __ldg(twl + q * j));
-    }
+    for (int q = 1; q < RADL; ++q) x[q] = cmul(x[q], tlast[(q - 1) * NS + j]);
     Dft<Cx, RADL>::run(x);
     const int k2 = c0 + c;
     Cx* zs = sr ? zb : za;
+    const Cx wj = ta[c * NS + j];
 #pragma unroll
     for (int q = 0; q < RADL; ++q) {
       const int p1 = j + q * NS;
-      const Cx w = twiddle<R>(a.tw, L, (uint32_t)p1 * (uint32_t)k2);
+      const Cx w = q == 0 ? wj : cmul(wj, tb[c * RADL + q]);
       zs[((int64_t)(p1 >> lr) * N2 + k2) * RRr + (p1 & (RRr - 1))] = cmul(x[q], w);
     }
   }
 }
 
 template <typename R, int L1, int C, int NT, int SRC, int TAPS>
-__global__ void __launch_bounds__(NT, (min_blocks<R, L1, C>())) k_cols(ColsArgs<R> a) {
+__global__ void __launch_bounds__(NT, (blocks_for_smem(cols_smem<R, L1, C>()))) k_cols(ColsArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[96];
   const int t = a.ti >= 0 ? a.ti : (int)blockIdx.y;
@@ -205,7 +250,12 @@ __device__ __forceinline__ void rows_tile(const RowsArgs<R>& a, int t, int blk, 
   // there: lanes run over r, then j, so the loads are contiguous.
   const Cx* za = zbase + (int64_t)blk * N2 * RR;
   const Cx* zb = za + ((int64_t)1 << L);
-  constexpr int RB0 = 4;
+  using PB = PlanB<L2>;
+  Cx* tws = buf + 2 * RR * STRIDE;        // shared-memory stages
+  Cx* tlast = tws + PB::MID_TW;           // last stage, [q - 1][j]
+  build_mid_tw<R, L2, PB::RB0, PB::NSL_LAST, NT>(tws, a.tw.tl[L2]);
+  build_stage_tw<R, L2, PB::NSL_LAST, PB::RBL, NT>(tlast, a.tw.tl[L2]);
+  constexpr int RB0 = PB::RB0;
   constexpr int RAD0 = 1 << RB0;
   constexpr int Q0 = N2 / RAD0;                   // butterflies per sequence
   constexpr int UNITS0 = 2 * RR * Q0;
@@ -227,10 +277,9 @@ __device__ __forceinline__ void rows_tile(const RowsArgs<R>& a, int t, int blk, 
   __syncthreads();
   // middle stages in shared memory; the last stage (radix <= 8) pairs the
   // a and b series of the same butterfly so that 2F is formed in registers
-  constexpr int REM = L2 - RB0;
-  constexpr int RBL = REM >= 3 ? 3 : REM;
-  constexpr int NSL_LAST = L2 - RBL;
-  fft_mid_stages<R, L2, RB0, NSL_LAST, NT, 2 * RR, STRIDE>(buf, a.tw.tl[L2]);
+  constexpr int RBL = PB::RBL;
+  constexpr int NSL_LAST = PB::NSL_LAST;
+  fft_mid_stages<R, L2, RB0, NSL_LAST, NT, 2 * RR, STRIDE>(buf, tws);
   R ca, cb, cc;
   if constexpr (std::is_same<R, float>::value) {
     ca = m.ca; cb = m.cb; cc = m.cc;
@@ -239,9 +288,8 @@ __device__ __forceinline__ void rows_tile(const RowsArgs<R>& a, int t, int blk, 
     const double sc = 1.0 / (a.pc.sigma2 * D);
     ca = 2.0 * m.B * sc; cb = 2.0 * m.A * sc; cc = -4.0 * m.C * sc;
   }
-  constexpr int RADL = 1 << RBL;
-  constexpr int NS = N2 / RADL;
-  const Cx* twl = a.tw.tl[L2];
+  constexpr int RADL = PB::RADL;
+  constexpr int NS = PB::NS;
 #pragma unroll 1
   for (int u = threadIdx.x; u < RR * NS; u += NT) {
     const int r = u & (RR - 1);
@@ -254,7 +302,7 @@ __device__ __forceinline__ void rows_tile(const RowsArgs<R>& a, int t, int blk, 
     }
 #pragma unroll
     for (int q = 1; q < RADL; ++q) {
-      const Cx w = __ldg(twl + q * j);
+      const Cx w = tlast[(q - 1) * NS + j];
       fa[q] = cmul(fa[q], w);
       fb[q] = cmul(fb[q], w);
     }
@@ -271,7 +319,7 @@ __device__ __forceinline__ void rows_tile(const RowsArgs<R>& a, int t, int blk, 
 }
 
 template <typename R, int L2, int RR, int NT>
-__global__ void __launch_bounds__(NT, (min_blocks<R, L2, RR>())) k_rows(RowsArgs<R> a) {
+__global__ void __launch_bounds__(NT, (blocks_for_smem(rows_smem<R, L2, RR>()))) k_rows(RowsArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int t = a.ti >= 0 ? a.ti : (int)blockIdx.y;
   const TmplMeta& m = a.c.meta[t];

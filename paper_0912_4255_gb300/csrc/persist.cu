@@ -218,10 +218,11 @@ cudaError_t launch_persist_t(const PersistArgs& p, cudaStream_t s, size_t smem) 
 
 int persist_slots() { return kSlots; }
 
-// Largest dynamic shared memory of any tile shape (FP32).
+// Largest dynamic shared memory of any tile shape of either pass (FP32).
 size_t persist_smem() {
   size_t m = 0;
-#define FS_P_SM(V) { const size_t a = smem_for<float, V, 2 * cols_for<float>(V), cols_for<float>(V)>(); if (a > m) m = a; }
+#define FS_P_SM(V) { const size_t a = cols_smem<float, V, cols_for<float>(V)>(), b = rows_smem<float, V, cols_for<float>(V)>(); \
+                       if (a > m) m = a; if (b > m) m = b; }
   FS_P_SM(6) FS_P_SM(7) FS_P_SM(8) FS_P_SM(9) FS_P_SM(10) FS_P_SM(11) FS_P_SM(12)
 #undef FS_P_SM
   return m;

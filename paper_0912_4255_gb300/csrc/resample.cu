@@ -74,7 +74,106 @@ cudaError_t dispatch(const PlanConst& pc, const Chunk& c, int ti, int log2n, con
   return cudaGetLastError();
 }
 
+// Tiled form for the unfused path.  One block resamples a tile of TR rows x
+// TC consecutive columns of the N1 x N2 grid (grid point k = k2 + N2 k1), so
+// that a warp handles 32 consecutive grid points: one knot record for all
+// lanes, taps from one contiguous run of x.  The tile goes through shared
+// memory and is stored in the order in which the first FFT pass reads its
+// columns, W[k2 / C][k1][k2 % C], as runs of TR * C values.  Tiles that lie
+// wholly at k >= n_b store nothing: the first pass reads those points as
+// zero without loading them.
+template <typename R> constexpr int tile_points() { return std::is_same<R, float>::value ? 2048 : 1024; }
+
+template <typename R, int INTERP, int TAPS>
+__global__ void __launch_bounds__(kResThreads)
+k_resample_t(PlanConst pc, Chunk c, int l2, int lc, const float2* __restrict__ x,
+             const int64_t* __restrict__ gaps, const double* __restrict__ wcs, int* status) {
+  using Cx = cpx<R>;
+  using Knot = typename KnotOf<R>::T;
+  constexpr int P = tile_points<R>();
+  constexpr int LP = std::is_same<R, float>::value ? 11 : 10;
+  __shared__ double red[96];
+  __shared__ Cx sa[P + 32], sb[P + 32];
+  const int t = blockIdx.y;
+  const TmplMeta& m = c.meta[t];
+  if (m.status != FSTAT_OK) return;
+  const int L = m.log2n;
+  const int nblk = 1 << (L - LP);
+  if ((int)blockIdx.x >= nblk) return;
+  const int ltc = l2 < 8 ? l2 : 8;             // log2 TC
+  const int TC = 1 << ltc;
+  const int TR = P >> ltc;
+  const int c0 = ((int)blockIdx.x & ((1 << (l2 - ltc)) - 1)) << ltc;
+  const int r0 = ((int)blockIdx.x >> (l2 - ltc)) * TR;
+  const int n_b = (int)m.n_b;
+  const bool live = c0 + (r0 << l2) < n_b;
+  float pa = 0.f, pb = 0.f, pcc = 0.f;
+  if (live) {
+    const Knot* kn = reinterpret_cast<const Knot*>(c.knots) + (int64_t)t * c.knot_stride;
+    GapCursor gc = make_cursor(m, gaps);
+#pragma unroll 1
+    for (int e = threadIdx.x; e < P; e += kResThreads) {
+      const int col = e & (TC - 1), row = e >> ltc;
+      const int k = c0 + col + ((r0 + row) << l2);
+      Cx va = czero<Cx>(), vb = czero<Cx>();
+      if (k < n_b) {
+        R aa, bb;
+        if (sample_weights<R, INTERP, TAPS>(pc, kn, k, x, gc, wcs, va, vb, aa, bb)) {
+          pa += (float)(aa * aa); pb += (float)(bb * bb); pcc += (float)(aa * bb);
+        }
+      }
+      sa[row * (TC + 1) + col] = va;
+      sb[row * (TC + 1) + col] = vb;
+    }
+  }
+  double sA, sB, sC;
+  block_sum3(pa, pb, pcc, sA, sB, sC, red);     // also orders the tile writes before the reads below
+  double* part = c.partials + (int64_t)t * c.part_stride * 3;
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x] = sA; part[3 * blockIdx.x + 1] = sB; part[3 * blockIdx.x + 2] = sC;
+  }
+  if (live) {
+    Cx* wa = reinterpret_cast<Cx*>(c.wa) + (int64_t)t * c.z_stride;
+    Cx* wb = wa + ((int64_t)1 << L);
+    const int lrun = (LP - ltc) + lc;            // log2 (TR * C)
+    const int64_t gstride = (int64_t)1 << (L - l2 + lc);   // N1 * C
+#pragma unroll 4
+    for (int e = threadIdx.x; e < P; e += kResThreads) {
+      const int g = e >> lrun, w = e & ((1 << lrun) - 1);
+      const int row = w >> lc, col = (g << lc) + (w & ((1 << lc) - 1));
+      const int64_t o = ((int64_t)(c0 >> lc) + g) * gstride + ((int64_t)r0 << lc) + w;
+      __stcs(wa + o, sa[row * (TC + 1) + col]);
+      __stcs(wb + o, sb[row * (TC + 1) + col]);
+    }
+  }
+  finalize_sums(c.meta + t, part, nblk, c.counters + t, pc.sigma2, nullptr, status);
+}
+
 }  // namespace
+
+cudaError_t launch_resample_t(const PlanConst& pc, const Chunk& c, const Shape& sh, const float2* x,
+                              const int64_t* gaps, const double* wcs, int* status, cudaStream_t s) {
+  int lc = 0;
+  while ((1 << lc) < sh.cols) ++lc;
+  if (pc.precision == FSTAT_PREC_FP64) {
+    dim3 grid((unsigned)(((int64_t)1 << sh.log2n) / tile_points<double>()), (unsigned)c.nt);
+    if (pc.interp == FSTAT_NEAREST)
+      k_resample_t<double, FSTAT_NEAREST, 8><<<grid, kResThreads, 0, s>>>(pc, c, sh.l2, lc, x, gaps, wcs, status);
+    else if (pc.taps == 8)
+      k_resample_t<double, FSTAT_SINC, 8><<<grid, kResThreads, 0, s>>>(pc, c, sh.l2, lc, x, gaps, wcs, status);
+    else
+      k_resample_t<double, FSTAT_SINC, 0><<<grid, kResThreads, 0, s>>>(pc, c, sh.l2, lc, x, gaps, wcs, status);
+    return cudaGetLastError();
+  }
+  dim3 grid((unsigned)(((int64_t)1 << sh.log2n) / tile_points<float>()), (unsigned)c.nt);
+  if (pc.interp == FSTAT_NEAREST)
+    k_resample_t<float, FSTAT_NEAREST, 8><<<grid, kResThreads, 0, s>>>(pc, c, sh.l2, lc, x, gaps, wcs, status);
+  else if (pc.taps == 8)
+    k_resample_t<float, FSTAT_SINC, 8><<<grid, kResThreads, 0, s>>>(pc, c, sh.l2, lc, x, gaps, wcs, status);
+  else
+    k_resample_t<float, FSTAT_SINC, 0><<<grid, kResThreads, 0, s>>>(pc, c, sh.l2, lc, x, gaps, wcs, status);
+  return cudaGetLastError();
+}
 
 // out_double: 0 -> complex64 output, 1 -> complex128 output (FP64 internal buffers)
 cudaError_t launch_resample_w(const PlanConst& pc, const Chunk& c, int ti, int log2n, const float2* x,

@@ -19,7 +19,7 @@ cudaError_t FS_CAT(rows, FS_REAL, FS_L2)(const RowsArgs<FS_REAL>& a, dim3 grid, 
   constexpr int L2 = FS_L2;
   constexpr int RR = cols_for<R>(L2);
   constexpr int NT = threads_for<R>(L2, 2 * RR);
-  constexpr size_t SM = smem_for<R, L2, 2 * RR, RR>();
+  constexpr size_t SM = rows_smem<R, L2, RR>();
   auto kern = k_rows<R, L2, RR, NT>;
   static int attr_done = 0;
   if (!attr_done) {

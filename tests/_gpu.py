@@ -8,6 +8,8 @@ from oracle import inject as I
 from oracle import resample as R
 
 NOGAPS = np.zeros((0, 2), np.int64)
+# FSTAT_MODE_* of include/fstat.h
+MODES = {"fused": 0, "plain": 1, "persistent": 2, "split": 3}
 
 
 def r15(got, ref):

@@ -10,7 +10,7 @@ import synth
 from oracle import fstat as F
 from oracle import resample as R
 
-from _gpu import (NOGAPS, injected_series, oracle_two_f, r15, run_compute, run_resample,
+from _gpu import (MODES, NOGAPS, injected_series, oracle_two_f, r15, run_compute, run_resample,
                   tie_margin)
 
 pytestmark = pytest.mark.gpu
@@ -57,9 +57,11 @@ def test_resample_stage_matches_oracle_series(interp):
         np.testing.assert_allclose(abcd[i, 3], A * B - C * C, rtol=1e-5)
 
 
-def test_sinc_with_gaps_several_templates():
+@pytest.mark.parametrize("mode", ["fused", "split"])
+def test_sinc_with_gaps_several_templates(mode):
     """3 d of data, FFT 2^19, 8-tap Lanczos sinc, gaps, uneven spans and
-    spindowns in one batched launch."""
+    spindowns in one batched launch (resampling fused into the first FFT
+    pass, or tiled through memory)."""
     d = synth.PlanDesc(dt=0.5, n_data=3 * 172800 // 2 * 2, n_fft=1 << 19, interp=R.SINC,
                        f_het=300.0, max_templates=6)
     gaps = synth.gap_intervals(d.n_data, 0.1, 7200, 43200 // 2, seed=31)
@@ -71,28 +73,35 @@ def test_sinc_with_gaps_several_templates():
     ss = [0, 0, 5000, 0, 20000, 777]
     sl = [d.n_data, d.n_data, 200000, 259200, 150001, 250000]
     tm = synth.make_templates(al, de, fd, ss, sl, 0, len(gaps))
-    got, rc = run_compute(d, x, tm, gaps)
+    got, rc = run_compute(d, x, tm, gaps, mode=MODES[mode])
     assert rc == 0
     for i in range(len(tm)):
         ref = oracle_two_f(d, x, tm[i], gaps)
         assert r15(got[i], ref) <= TOL, i
 
 
-def test_plain_and_fused_agree():
+@pytest.mark.parametrize("mode", ["plain", "split"])
+@pytest.mark.parametrize("interp", [R.NEAREST, R.SINC])
+def test_unfused_and_fused_agree(mode, interp):
+    """The tiled resampler + load-mode first pass against the fused pass, at
+    a shape whose first-pass block holds several columns (2^17 = 2^9 x 2^8:
+    the column tiles and the tile of the resampler differ)."""
     import paper_0912_4255_gb300 as fs
-    d = synth.PlanDesc(dt=0.5, n_data=60000, n_fft=1 << 16, interp=R.SINC, f_het=80.0,
-                       max_templates=2)
+    d = synth.PlanDesc(dt=0.5, n_data=60000, n_fft=1 << 17, interp=interp, f_het=80.0,
+                       max_templates=3)
     x, _ = injected_series(d, 3, [synth.random_injection(4, df=0.3)])
-    tm = synth.make_templates([1.0, 2.0], [0.3, -0.3], [0.0, -2e-9], 0, d.n_data)
+    tm = synth.make_templates([1.0, 2.0, 4.0], [0.3, -0.3, 1.0], [0.0, -2e-9, -1e-8], [0, 0, 999],
+                              [d.n_data, d.n_data, 41001])
     a, rc1 = run_compute(d, x, tm, mode=fs.MODE_FUSED)
-    b, rc2 = run_compute(d, x, tm, mode=fs.MODE_PLAIN)
+    b, rc2 = run_compute(d, x, tm, mode=MODES[mode])
     assert rc1 == 0 and rc2 == 0
     assert r15(a, b) < 1e-6
-    for i in range(2):
+    for i in range(3):
         assert r15(b[i], oracle_two_f(d, x, tm[i])) <= TOL
 
 
-def test_fp64_mode_tight():
+@pytest.mark.parametrize("mode", ["fused", "split"])
+def test_fp64_mode_tight(mode):
     """All-FP64 path: agreement with the FP64 oracle to 1e-6 (the floor is the
     cubic interpolation of a, b between knots, ~1e-7, and the float32
     output)."""
@@ -100,19 +109,20 @@ def test_fp64_mode_tight():
                        precision=synth.PREC_FP64, max_templates=2)
     x, _ = injected_series(d, 5, [synth.random_injection(6, df=0.4, fdot=-5e-9)])
     tm = synth.make_templates([0.5, 4.4], [0.7, -0.1], [-5e-9, 0.0], 0, d.n_data)
-    got, rc = run_compute(d, x, tm)
+    got, rc = run_compute(d, x, tm, mode=MODES[mode])
     assert rc == 0
     for i in range(2):
         assert r15(got[i], oracle_two_f(d, x, tm[i])) <= 1e-6
 
 
-def test_invalid_template_reports_status_and_nan():
+@pytest.mark.parametrize("mode", ["fused", "split"])
+def test_invalid_template_reports_status_and_nan(mode):
     import paper_0912_4255_gb300 as fs
     d = synth.PlanDesc(dt=0.5, n_data=20000, n_fft=1 << 15, interp=R.NEAREST, max_templates=3)
     x = synth.complex_noise(d.n_data, 1.0, 9)
     tm = synth.make_templates([1.0, 1.0, 1.0], [0.2, 0.2, 0.2], 0.0,
                               [0, 15000, 0], [20000, 10000, 20000])
-    got, rc = run_compute(d, x, tm)
+    got, rc = run_compute(d, x, tm, mode=MODES[mode])
     assert rc == fs._lib.FSTAT_ERANGE
     assert np.all(np.isfinite(got[0])) and np.all(np.isnan(got[1])) and np.all(np.isfinite(got[2]))
     assert r15(got[2], oracle_two_f(d, x, tm[2])) <= TOL
