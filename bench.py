@@ -37,7 +37,7 @@ import synth  # noqa: E402
 N_SKY, N_FDOT = 1024, 8
 GAP_FRAC = 0.10
 BATCH = 64            # templates per fstat_compute call (the 2F ring buffer)
-KINDS = ("timemap", "resample", "fft_cols", "fft_rows", "grad_fwd", "grad_adj", "persistent")
+KINDS = ("timemap", "resample", "fft_cols", "fft_rows", "grad_fwd", "grad_adj", "persistent", "sums")
 
 
 def workload(rank: int = 0, world: int = 1):
@@ -174,7 +174,7 @@ def algorithmic_per_template(desc, fused=True):
     fft_a = 2 * 5 * n * l1 + 2 * 6 * n
     res = nb * (taps * 9 + 16)
     rows = 2 * 5 * n * l2 + 12 * n
-    out = {"fft_rows": (rows, 4.0 * n), "timemap": (0.0, 80.0 * (n >> 10)),
+    out = {"fft_rows": (rows, 4.0 * n), "timemap": (0.0, 80.0 * (n >> 10)), "sums": (0.0, 0.0),
            "persistent": (fft_a + res + rows, 8.0 * desc.n_data + 4.0 * n)}
     if fused:
         out["fft_cols"] = (fft_a + res, 8.0 * desc.n_data)
@@ -249,7 +249,7 @@ def main():
                     help="templates per GPU per step (default: the whole 8192-template grid)")
     ap.add_argument("--batch", type=int, default=BATCH,
                     help="templates per fstat_compute call (size of the 2F ring buffer)")
-    ap.add_argument("--mode", default="fused", choices=["fused", "split", "persistent", "plain"],
+    ap.add_argument("--mode", default="split", choices=["fused", "split", "persistent", "plain"],
                     help="library execution mode")
     ap.add_argument("--chunk", type=int, default=0,
                     help="templates per internal launch (0: the library's default)")
@@ -291,7 +291,7 @@ def main():
     plan = fs.Plan(desc, device=dev)
     mode = {"fused": fs.MODE_FUSED, "split": fs.MODE_SPLIT, "persistent": fs.MODE_PERSISTENT,
             "plain": fs.MODE_PLAIN}[args.mode]
-    if args.chunk or mode != fs.MODE_FUSED:
+    if args.chunk or mode != fs.MODE_SPLIT:
         plan.set_tuning(mode=mode, chunk=args.chunk)
     stream = torch.cuda.Stream(device=dev)
     x = torch.from_numpy(x_np.astype(np.complex64)).to(dev)
@@ -347,7 +347,7 @@ def main():
     peak_tf = fp32_peak_tflops(sm_mhz)
     per_tpl = algorithmic_per_template(desc, fused=mode in (fs.MODE_FUSED, fs.MODE_PERSISTENT))
     kernels = {}
-    for k in ("timemap", "resample", "fft_cols", "fft_rows", "persistent"):
+    for k in ("timemap", "resample", "fft_cols", "fft_rows", "persistent", "sums"):
         k_ms, k_n = prof[k]
         if not k_n:
             continue

@@ -70,7 +70,7 @@ enum {
   FSTAT_PREC_FP64  = 1, /* FP64 everywhere (time map, interpolation, FFT)   */
   FSTAT_PREC_FP32  = 2  /* FP32 everywhere, for the precision study         */
 };
-/* execution mode (fstat_tuning.mode) */
+/* execution mode (fstat_tuning.mode; a new plan starts in FSTAT_MODE_SPLIT) */
 enum {
   FSTAT_MODE_FUSED      = 0, /* resample+weight fused into the first FFT pass, batched grids */
   FSTAT_MODE_PLAIN      = 1, /* FSTAT_MODE_SPLIT one template per launch                      */
@@ -198,7 +198,8 @@ int fstat_grad(fstat_plan_t p, const float *x_h, const fstat_template *templates
  * on the call's stream around every kernel it launches.  fstat_profile_read
  * waits for the recorded events and returns, per kernel kind (0 time map,
  * 1 resample stage, 2 first FFT pass, 3 second FFT pass, 4 gradient
- * forward, 5 gradient adjoint, 6 persistent batch), the summed device
+ * forward, 5 gradient adjoint, 6 persistent batch, 7 the reduction of A, B,
+ * C after the unfused resample stage), the summed device
  * milliseconds and the number of launches since the last read, then clears
  * them.  Launch counts are kept whether or not timing is enabled.  ms and
  * launches are host arrays of n_kinds entries (n_kinds <= 8). */

@@ -113,7 +113,7 @@ class Plan:
         _check(self.lib.fstat_set_workspace(self.handle, ctypes.c_void_p(ws.data_ptr() + off),
                                             ws.numel() - off), "fstat_set_workspace")
 
-    def set_tuning(self, mode=MODE_FUSED, log2_n1=0, cols=0, rows=0, chunk=0, knot_log2=0):
+    def set_tuning(self, mode=MODE_SPLIT, log2_n1=0, cols=0, rows=0, chunk=0, knot_log2=0):
         need = ctypes.c_size_t()
         t = _lib.Tuning(mode, log2_n1, cols, rows, chunk, knot_log2)
         _check(self.lib.fstat_set_tuning(self.handle, ctypes.byref(t), ctypes.byref(need)),
@@ -213,7 +213,7 @@ def fstat_grad(plan: Plan, x_h, templates, df, gaps=None, stream=None):
     return twoF, grad
 
 
-KERNEL_KINDS = ("timemap", "resample", "fft_cols", "fft_rows", "grad_fwd", "grad_adj", "persistent")
+KERNEL_KINDS = ("timemap", "resample", "fft_cols", "fft_rows", "grad_fwd", "grad_adj", "persistent", "sums")
 
 
 def fstat_profile(plan: Plan, enable: bool = True):

@@ -15,7 +15,8 @@ using namespace fs;
 
 namespace {
 constexpr int kKinds = 8;
-enum { K_TIMEMAP = 0, K_RESAMPLE = 1, K_COLS = 2, K_ROWS = 3, K_GRADF = 4, K_GRADB = 5, K_PERSIST = 6 };
+enum { K_TIMEMAP = 0, K_RESAMPLE = 1, K_COLS = 2, K_ROWS = 3, K_GRADF = 4, K_GRADB = 5, K_PERSIST = 6,
+       K_SUMS = 7 };
 }
 
 struct fstat_plan_s {
@@ -299,7 +300,7 @@ int fstat_plan(fstat_plan_t* out, const fstat_plan_desc* d, size_t* workspace_by
   p->log2n = ilog2(d->n_fft);
   p->rec_bytes = d->precision == FSTAT_PREC_FP64 ? (int)sizeof(KnotD) : (int)sizeof(KnotF);
   p->cplx_bytes = d->precision == FSTAT_PREC_FP64 ? 16 : 8;
-  p->tune.mode = FSTAT_MODE_FUSED;
+  p->tune.mode = FSTAT_MODE_SPLIT;
   p->spin_limit = 1 << 22;        // x ~256 ns sleeps: about a second
   p->stall_template = -1;
   rc = choose_shape(p);
@@ -415,8 +416,10 @@ int fstat_compute(fstat_plan_t p, const float* x_h, const fstat_template* t, int
       e = timed(p, K_TIMEMAP, s, [&] { return launch_timemap(p->pc, c, p->log2n, p->tune.mode, gaps, n_gaps_total, p->status, t0, s); });
     if (e != cudaSuccess) return FSTAT_ECUDA;
     const int fused = p->tune.mode == FSTAT_MODE_FUSED;
-    if (!fused)
-      e = timed(p, K_RESAMPLE, s, [&] { return launch_resample_t(p->pc, c, p->sh, x, gaps, p->wcs, p->status, s); });
+    if (!fused) {
+      e = timed(p, K_RESAMPLE, s, [&] { return launch_resample_t(p->pc, c, p->sh, x, gaps, p->wcs, s); });
+      if (e == cudaSuccess) e = timed(p, K_SUMS, s, [&] { return launch_sums_t(p->pc, c, p->sh, p->status, s); });
+    }
     if (e == cudaSuccess)
       e = timed(p, K_COLS, s, [&] { return launch_cols_w(p->pc, c, p->sh, fused, -1, x, gaps, p->wcs, &p->twf, &p->twd, p->status, s); });
     if (e == cudaSuccess) e = timed(p, K_ROWS, s, [&] { return launch_rows_w(p->pc, c, p->sh, -1, &p->twf, &p->twd, twoF, s); });

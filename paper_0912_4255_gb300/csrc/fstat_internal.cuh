@@ -338,6 +338,89 @@ template <> __device__ __forceinline__ const float* win_table<float>(const doubl
   return reinterpret_cast<const float*>(wcs + 64);
 }
 
+__device__ __forceinline__ float rcp_approx(float v) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+}
+
+// Step 4 of Sec. III.A.2 with the 8-tap windowed sinc in single precision.
+// n0 = floor(u), f = u - n0 in [0, 1), qoff = (f >= 1/2), dn = f - qoff (so
+// that jnn = n0 + qoff is the nearest sample and dn = u - jnn).  Tap i
+// (i = 0..7, sample j = n0 - 3 + i) sits at x_i = f + 3 - i; the nearest tap
+// gets x = dn exactly (f - 1 is exact for f >= 1/2), so its weight and
+// sin(pi dn) come from the same number.  With s = sin(pi f):
+//   sin(pi x_i) = (-1)^(3-i) s,
+//   sin(pi x_i / 4) = sin(pi f/4) cos(pi (3-i)/4) + cos(pi f/4) sin(pi (3-i)/4),
+// and x_{i+4} = x_i - 4 turns sin(pi x / 4) into its negative.  Lanczos:
+// K(x) = 4 sin(pi x) sin(pi x/4) / (pi^2 x^2); plain truncation: sin(pi x)/(pi x).
+// The common factor s leaves the sum over taps.  Returns the mask (the
+// nearest sample is valid data); taps on invalid samples weigh zero.
+__device__ __forceinline__ bool sinc8_f32(const float2* __restrict__ x, GapCursor& gc, bool lanczos,
+                                          int n0, int qoff, float f, float dn, float2& z) {
+  const int jlo = n0 - 3;
+  const int jnn = n0 + qoff;
+  if (fabsf(dn) < 1e-7f) {
+    // u on a sample (to the precision of u): the interpolant is that sample
+    if (!gc.valid(jnn)) return false;
+    z = __ldg(x + jnn);
+    return true;
+  }
+  const bool full = gc.window_valid(jlo, jlo + 7);
+  float2 v[8];
+  if (full) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __ldg(x + jlo + i);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      int j = jlo + i;
+      j = j < gc.lo ? gc.lo : (j >= gc.hi ? gc.hi - 1 : j);
+      v[i] = __ldg(x + j);
+    }
+  }
+  // sin, cos of pi dn / 4 by the polynomial; sin(pi dn) by two doublings
+  float sh, ch;
+  sincospi_small(0.25f * dn, &sh, &ch);
+  const float s2 = 2.0f * sh * ch, c2 = fmaf(ch, ch, -sh * sh);
+  const float sdn = 2.0f * s2 * c2;
+  const float sf = qoff ? -sdn : sdn;                     // sin(pi f)
+  float g[8];
+  if (lanczos) {
+    // sin(pi x_i / 4) for i = 0..3: with p = (sin + cos)(pi dn/4) / sqrt 2 and
+    // m = (cos - sin)(pi dn/4) / sqrt 2 these are (m, cos, p, sin) for
+    // qoff = 0 and (-sin, m, cos, p) for qoff = 1 (f/4 = dn/4 + 1/4)
+    const float r2 = 0.70710678118654752f;
+    const float p = (sh + ch) * r2, m = (ch - sh) * r2;
+    const float w0 = qoff ? -sh : m, w1 = qoff ? m : ch, w2 = qoff ? ch : p, w3 = qoff ? p : sh;
+    // sign (-1)^(3-i) times the window, i = 0..3; taps 4..7 take the negatives
+    g[0] = -w0; g[1] = w1; g[2] = -w2; g[3] = w3;
+    g[4] = w0; g[5] = -w1; g[6] = w2; g[7] = -w3;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) g[i] = ((3 - i) & 1) ? -1.0f : 1.0f;
+  }
+  float2 acc = make_float2(0.f, 0.f);
+  bool msk = full;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float xi = f + (float)(3 - i);
+    float w = lanczos ? g[i] * rcp_approx(xi * xi) : g[i] * rcp_approx(xi);
+    if (!full) {
+      const bool ok = gc.valid(jlo + i);
+      if (jlo + i == jnn) msk = ok;
+      if (!ok) w = 0.0f;
+    }
+    acc.x = fmaf(w, v[i].x, acc.x);
+    acc.y = fmaf(w, v[i].y, acc.y);
+  }
+  if (!msk) return false;
+  const float sc = lanczos ? sf * (float)(4.0 / (3.14159265358979323846 * 3.14159265358979323846))
+                           : sf * (float)(1.0 / 3.14159265358979323846);
+  z = make_float2(acc.x * sc, acc.y * sc);
+  return true;
+}
+
 // Per-sample time map and weights (steps 2-5) at grid point k < N_b of a
 // template: returns the mask and writes wa = m a y, wb = m b y with
 // y = z(T^k) exp(-2 pi i P(k)), and the beam values a, b.
@@ -372,6 +455,21 @@ __device__ __forceinline__ bool sample_weights(
     a = q.a0 + ((q.a3 * s + q.a2) * s + q.a1) * s;
     b = q.b0 + ((q.b3 * s + q.b2) * s + q.b1) * s;
   }
+  C z;
+  if constexpr (std::is_same<R, float>::value && INTERP == FSTAT_SINC && TAPS == 8) {
+    // n0 = floor(u) = ibase + fl, f = dev - fl exactly
+    int fl_i;
+    float fl = round_nearest(dev, &fl_i);
+    if (fl > dev) { fl -= 1.0f; --fl_i; }
+    const float f = dev - fl;
+    const int qoff = f >= 0.5f ? 1 : 0;
+    const float dn = qoff ? f - 1.0f : f;
+    float2 zz;
+    if (!sinc8_f32(x, gc, pc.window == FSTAT_WIN_LANCZOS, ibase + fl_i, qoff, f, dn, zz)) {
+      wa = czero<C>(); wb = czero<C>(); return false;
+    }
+    z = zz;
+  } else {
   int jnn_off;                        // jnn - ibase = floor(dev + 1/2)
   R jnn_f;
   if constexpr (std::is_same<R, float>::value) {
@@ -384,7 +482,6 @@ __device__ __forceinline__ bool sample_weights(
     jnn_off = (int)jnn_f;
   }
   const int jnn = ibase + jnn_off;
-  C z;
   if constexpr (INTERP == FSTAT_NEAREST) {
     if (!gc.valid(jnn)) { wa = czero<C>(); wb = czero<C>(); return false; }
     z = ldx<R>(x, jnn);
@@ -502,6 +599,7 @@ __device__ __forceinline__ bool sample_weights(
       if (!msk) { wa = czero<C>(); wb = czero<C>(); return false; }
       z = acc;
     }
+  }
   }
   // remove exp(2 pi i P): multiply by exp(-2 pi i r), r = P - rint(P)
   C e;
@@ -704,6 +802,24 @@ __device__ __forceinline__ void block_sum3(float fx, float fy, float fz, double&
   }
 }
 
+// A, B, C (Eq. 8) of a template and the coefficients of 2F (Eq. 6 with
+// D = AB - C^2); a template without valid samples, or with a and b
+// proportional, gets FSTAT_ERANGE.
+__device__ __forceinline__ void set_sums(TmplMeta* meta, double A, double B, double Cc, double sigma2,
+                                         double* abcd, int* status) {
+  const double D = A * B - Cc * Cc;
+  meta->A = A; meta->B = B; meta->C = Cc;
+  if (!(D > 0.0) || !isfinite(D)) {
+    meta->status = FSTAT_ERANGE;
+    set_status(status, FSTAT_ERANGE);
+  }
+  const double s = 1.0 / (sigma2 * D);
+  meta->ca = (float)(2.0 * B * s);
+  meta->cb = (float)(2.0 * A * s);
+  meta->cc = (float)(-4.0 * Cc * s);
+  if (abcd) { abcd[0] = A; abcd[1] = B; abcd[2] = Cc; abcd[3] = D; }
+}
+
 // The last block of a template to finish its partial sums reduces them in
 // index order (deterministic) and fills A, B, C and the 2F coefficients.
 __device__ __forceinline__ void finalize_sums(TmplMeta* meta, const double* __restrict__ partials,
@@ -723,17 +839,7 @@ __device__ __forceinline__ void finalize_sums(TmplMeta* meta, const double* __re
       B += __ldcg(partials + 3 * i + 1);
       Cc += __ldcg(partials + 3 * i + 2);
     }
-    const double D = A * B - Cc * Cc;
-    meta->A = A; meta->B = B; meta->C = Cc;
-    if (!(D > 0.0) || !isfinite(D)) {       // no valid sample, or a and b proportional
-      meta->status = FSTAT_ERANGE;
-      set_status(status, FSTAT_ERANGE);
-    }
-    const double s = 1.0 / (sigma2 * D);
-    meta->ca = (float)(2.0 * B * s);
-    meta->cb = (float)(2.0 * A * s);
-    meta->cc = (float)(-4.0 * Cc * s);
-    if (abcd) { abcd[0] = A; abcd[1] = B; abcd[2] = Cc; abcd[3] = D; }
+    set_sums(meta, A, B, Cc, sigma2, abcd, status);
     *counter = 0;
   }
 }
@@ -768,7 +874,8 @@ cudaError_t launch_resample_w(const PlanConst& pc, const Chunk& c, int ti, int l
                               int64_t out_stride, int out_double, double* abcd, int* status,
                               cudaStream_t s);
 cudaError_t launch_resample_t(const PlanConst& pc, const Chunk& c, const Shape& sh, const float2* x,
-                              const int64_t* gaps, const double* wcs, int* status, cudaStream_t s);
+                              const int64_t* gaps, const double* wcs, cudaStream_t s);
+cudaError_t launch_sums_t(const PlanConst& pc, const Chunk& c, const Shape& sh, int* status, cudaStream_t s);
 cudaError_t launch_cols_w(const PlanConst& pc, const Chunk& c, const Shape& sh, int fused, int ti,
                           const float2* x, const int64_t* gaps, const double* wcs, const void* twf,
                           const void* twd, int* status, cudaStream_t s);

@@ -74,43 +74,67 @@ cudaError_t dispatch(const PlanConst& pc, const Chunk& c, int ti, int log2n, con
   return cudaGetLastError();
 }
 
-// Tiled form for the unfused path.  One block resamples a tile of TR rows x
-// TC consecutive columns of the N1 x N2 grid (grid point k = k2 + N2 k1), so
-// that a warp handles 32 consecutive grid points: one knot record for all
-// lanes, taps from one contiguous run of x.  The tile goes through shared
-// memory and is stored in the order in which the first FFT pass reads its
-// columns, W[k2 / C][k1][k2 % C], as runs of TR * C values.  Tiles that lie
-// wholly at k >= n_b store nothing: the first pass reads those points as
-// zero without loading them.
-template <typename R> constexpr int tile_points() { return std::is_same<R, float>::value ? 2048 : 1024; }
+// Tiled form for the unfused path.  A tile is TR rows x TC consecutive
+// columns of the N1 x N2 grid (grid point k = k2 + N2 k1), so that a warp
+// handles 32 consecutive grid points: one knot record for all lanes, taps
+// from one contiguous run of x.  The tile goes through shared memory and is
+// stored in the order in which the first FFT pass reads its columns,
+// W[k2 / C][k1][k2 % C], as runs of TR * C values.  Tiles are numbered by
+// row tile, then column tile, so that their first point c0 + r0 N2 grows
+// with the number: the tiles holding points below n_b are a prefix, and the
+// first pass reads every point at k >= n_b as zero without loading it.  Each
+// tile leaves its partial sums of A, B, C; k_sums_t reduces them.
+template <typename R> constexpr int tile_log2() { return std::is_same<R, float>::value ? 11 : 10; }
+constexpr int kTilesPerBlock = 4;
+
+__host__ __device__ __forceinline__ int tile_log2_cols(int l2) { return l2 < 8 ? l2 : 8; }
+
+// number of tiles with a point below n_b
+__host__ __device__ __forceinline__ int live_tiles(int64_t n_b, int l2, int lp) {
+  if (n_b <= 0) return 0;
+  const int ltc = tile_log2_cols(l2);
+  const int64_t span = (int64_t)1 << (lp - ltc + l2);    // points of one row tile, TR N2
+  const int ncol = 1 << (l2 - ltc);
+  const int64_t rt = (n_b - 1) / span;
+  const int64_t rem = n_b - rt * span;
+  const int64_t ct = (rem + (1 << ltc) - 1) >> ltc;
+  return (int)(rt * ncol + (ct < ncol ? ct : ncol));
+}
 
 template <typename R, int INTERP, int TAPS>
 __global__ void __launch_bounds__(kResThreads)
 k_resample_t(PlanConst pc, Chunk c, int l2, int lc, const float2* __restrict__ x,
-             const int64_t* __restrict__ gaps, const double* __restrict__ wcs, int* status) {
+             const int64_t* __restrict__ gaps, const double* __restrict__ wcs) {
   using Cx = cpx<R>;
   using Knot = typename KnotOf<R>::T;
-  constexpr int P = tile_points<R>();
-  constexpr int LP = std::is_same<R, float>::value ? 11 : 10;
+  constexpr int LP = tile_log2<R>();
+  constexpr int P = 1 << LP;
   __shared__ double red[96];
   __shared__ Cx sa[P + 32], sb[P + 32];
   const int t = blockIdx.y;
   const TmplMeta& m = c.meta[t];
   if (m.status != FSTAT_OK) return;
   const int L = m.log2n;
-  const int nblk = 1 << (L - LP);
-  if ((int)blockIdx.x >= nblk) return;
-  const int ltc = l2 < 8 ? l2 : 8;             // log2 TC
+  const int n_b = (int)m.n_b;
+  const int nlive = live_tiles(m.n_b, l2, LP);
+  const int ltc = tile_log2_cols(l2);          // log2 TC
   const int TC = 1 << ltc;
   const int TR = P >> ltc;
-  const int c0 = ((int)blockIdx.x & ((1 << (l2 - ltc)) - 1)) << ltc;
-  const int r0 = ((int)blockIdx.x >> (l2 - ltc)) * TR;
-  const int n_b = (int)m.n_b;
-  const bool live = c0 + (r0 << l2) < n_b;
-  float pa = 0.f, pb = 0.f, pcc = 0.f;
-  if (live) {
-    const Knot* kn = reinterpret_cast<const Knot*>(c.knots) + (int64_t)t * c.knot_stride;
-    GapCursor gc = make_cursor(m, gaps);
+  const Knot* kn = reinterpret_cast<const Knot*>(c.knots) + (int64_t)t * c.knot_stride;
+  double* part = c.partials + (int64_t)t * c.part_stride * 3;
+  Cx* wa = reinterpret_cast<Cx*>(c.wa) + (int64_t)t * c.z_stride;
+  Cx* wb = wa + ((int64_t)1 << L);
+  const int lrun = (LP - ltc) + lc;            // log2 (TR * C)
+  const int64_t gstride = (int64_t)1 << (L - l2 + lc);   // N1 * C
+  GapCursor gc = make_cursor(m, gaps);
+#pragma unroll 1
+  for (int tt = 0; tt < kTilesPerBlock; ++tt) {
+    const int b = (int)blockIdx.x * kTilesPerBlock + tt;
+    if (b >= nlive) break;
+    const int c0 = (b & ((1 << (l2 - ltc)) - 1)) << ltc;
+    const int r0 = (b >> (l2 - ltc)) * TR;
+    if (tt > 0) gc = make_cursor(m, gaps);    // the points of a new tile start lower
+    float pa = 0.f, pb = 0.f, pcc = 0.f;
 #pragma unroll 1
     for (int e = threadIdx.x; e < P; e += kResThreads) {
       const int col = e & (TC - 1), row = e >> ltc;
@@ -125,18 +149,9 @@ k_resample_t(PlanConst pc, Chunk c, int l2, int lc, const float2* __restrict__ x
       sa[row * (TC + 1) + col] = va;
       sb[row * (TC + 1) + col] = vb;
     }
-  }
-  double sA, sB, sC;
-  block_sum3(pa, pb, pcc, sA, sB, sC, red);     // also orders the tile writes before the reads below
-  double* part = c.partials + (int64_t)t * c.part_stride * 3;
-  if (threadIdx.x == 0) {
-    part[3 * blockIdx.x] = sA; part[3 * blockIdx.x + 1] = sB; part[3 * blockIdx.x + 2] = sC;
-  }
-  if (live) {
-    Cx* wa = reinterpret_cast<Cx*>(c.wa) + (int64_t)t * c.z_stride;
-    Cx* wb = wa + ((int64_t)1 << L);
-    const int lrun = (LP - ltc) + lc;            // log2 (TR * C)
-    const int64_t gstride = (int64_t)1 << (L - l2 + lc);   // N1 * C
+    double sA, sB, sC;
+    block_sum3(pa, pb, pcc, sA, sB, sC, red);   // also orders the tile writes before the reads below
+    if (threadIdx.x == 0) { part[3 * b] = sA; part[3 * b + 1] = sB; part[3 * b + 2] = sC; }
 #pragma unroll 4
     for (int e = threadIdx.x; e < P; e += kResThreads) {
       const int g = e >> lrun, w = e & ((1 << lrun) - 1);
@@ -145,33 +160,92 @@ k_resample_t(PlanConst pc, Chunk c, int l2, int lc, const float2* __restrict__ x
       __stcs(wa + o, sa[row * (TC + 1) + col]);
       __stcs(wb + o, sb[row * (TC + 1) + col]);
     }
+    __syncthreads();                            // before the next tile overwrites sa, sb
   }
-  finalize_sums(c.meta + t, part, nblk, c.counters + t, pc.sigma2, nullptr, status);
+}
+
+// One block per template: A, B, C from the partials of its tiles, summed in
+// FP64 in a fixed order (deterministic).  covered: tiles the resampling grid
+// reached; a template with more tiles below n_b (not expected: the grid is
+// sized from a bound on n_b) is reported as FSTAT_ERANGE.
+constexpr int kSumThreads = 256;
+__global__ void __launch_bounds__(kSumThreads)
+k_sums_t(Chunk c, int l2, int lp, int covered, double sigma2, int* status) {
+  __shared__ double sh[3][kSumThreads];
+  TmplMeta* m = c.meta + blockIdx.x;
+  if (m->status != FSTAT_OK) return;
+  const int nlive = live_tiles(m->n_b, l2, lp);
+  if (nlive > covered) {
+    if (threadIdx.x == 0) { m->status = FSTAT_ERANGE; set_status(status, FSTAT_ERANGE); }
+    return;
+  }
+  const double* part = c.partials + (int64_t)blockIdx.x * c.part_stride * 3;
+  double A = 0, B = 0, Cc = 0;
+  for (int i = threadIdx.x; i < nlive; i += kSumThreads) {
+    A += part[3 * i]; B += part[3 * i + 1]; Cc += part[3 * i + 2];
+  }
+  sh[0][threadIdx.x] = A; sh[1][threadIdx.x] = B; sh[2][threadIdx.x] = Cc;
+  __syncthreads();
+  for (int h = kSumThreads / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + h];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + h];
+      sh[2][threadIdx.x] += sh[2][threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) set_sums(m, sh[0][0], sh[1][0], sh[2][0], sigma2, nullptr, status);
+}
+
+// Upper bound on n_b for every template of the plan: t_b = t + t_m(t) and
+// |dt_m/dt| <= (2 pi / year) au / c + (2 pi / sidereal day) R / c, so a span
+// of n_data samples maps to at most (n_data - 1)(1 + beta) + 1 grid points.
+int64_t nb_bound(const PlanConst& pc, int64_t n_fft) {
+  const double beta = pc.wo * pc.auc + pc.ws * pc.rc;
+  const double b = (double)(pc.n_data - 1) * (1.0 + 1.01 * beta + 1e-12) + 3.0;
+  const int64_t nb = (int64_t)b;
+  return nb < n_fft ? nb : n_fft;
+}
+
+template <typename R>
+int resample_blocks(const PlanConst& pc, const Shape& sh) {
+  const int covered = live_tiles(nb_bound(pc, (int64_t)1 << sh.log2n), sh.l2, tile_log2<R>());
+  return (covered + kTilesPerBlock - 1) / kTilesPerBlock;
 }
 
 }  // namespace
 
 cudaError_t launch_resample_t(const PlanConst& pc, const Chunk& c, const Shape& sh, const float2* x,
-                              const int64_t* gaps, const double* wcs, int* status, cudaStream_t s) {
+                              const int64_t* gaps, const double* wcs, cudaStream_t s) {
   int lc = 0;
   while ((1 << lc) < sh.cols) ++lc;
   if (pc.precision == FSTAT_PREC_FP64) {
-    dim3 grid((unsigned)(((int64_t)1 << sh.log2n) / tile_points<double>()), (unsigned)c.nt);
+    dim3 grid((unsigned)resample_blocks<double>(pc, sh), (unsigned)c.nt);
+    if (grid.x == 0) return cudaSuccess;
     if (pc.interp == FSTAT_NEAREST)
-      k_resample_t<double, FSTAT_NEAREST, 8><<<grid, kResThreads, 0, s>>>(pc, c, sh.l2, lc, x, gaps, wcs, status);
+      k_resample_t<double, FSTAT_NEAREST, 8><<<grid, kResThreads, 0, s>>>(pc, c, sh.l2, lc, x, gaps, wcs);
     else if (pc.taps == 8)
-      k_resample_t<double, FSTAT_SINC, 8><<<grid, kResThreads, 0, s>>>(pc, c, sh.l2, lc, x, gaps, wcs, status);
+      k_resample_t<double, FSTAT_SINC, 8><<<grid, kResThreads, 0, s>>>(pc, c, sh.l2, lc, x, gaps, wcs);
     else
-      k_resample_t<double, FSTAT_SINC, 0><<<grid, kResThreads, 0, s>>>(pc, c, sh.l2, lc, x, gaps, wcs, status);
+      k_resample_t<double, FSTAT_SINC, 0><<<grid, kResThreads, 0, s>>>(pc, c, sh.l2, lc, x, gaps, wcs);
     return cudaGetLastError();
   }
-  dim3 grid((unsigned)(((int64_t)1 << sh.log2n) / tile_points<float>()), (unsigned)c.nt);
+  dim3 grid((unsigned)resample_blocks<float>(pc, sh), (unsigned)c.nt);
+  if (grid.x == 0) return cudaSuccess;
   if (pc.interp == FSTAT_NEAREST)
-    k_resample_t<float, FSTAT_NEAREST, 8><<<grid, kResThreads, 0, s>>>(pc, c, sh.l2, lc, x, gaps, wcs, status);
+    k_resample_t<float, FSTAT_NEAREST, 8><<<grid, kResThreads, 0, s>>>(pc, c, sh.l2, lc, x, gaps, wcs);
   else if (pc.taps == 8)
-    k_resample_t<float, FSTAT_SINC, 8><<<grid, kResThreads, 0, s>>>(pc, c, sh.l2, lc, x, gaps, wcs, status);
+    k_resample_t<float, FSTAT_SINC, 8><<<grid, kResThreads, 0, s>>>(pc, c, sh.l2, lc, x, gaps, wcs);
   else
-    k_resample_t<float, FSTAT_SINC, 0><<<grid, kResThreads, 0, s>>>(pc, c, sh.l2, lc, x, gaps, wcs, status);
+    k_resample_t<float, FSTAT_SINC, 0><<<grid, kResThreads, 0, s>>>(pc, c, sh.l2, lc, x, gaps, wcs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sums_t(const PlanConst& pc, const Chunk& c, const Shape& sh, int* status, cudaStream_t s) {
+  const bool d = pc.precision == FSTAT_PREC_FP64;
+  const int lp = d ? tile_log2<double>() : tile_log2<float>();
+  const int covered = (d ? resample_blocks<double>(pc, sh) : resample_blocks<float>(pc, sh)) * kTilesPerBlock;
+  k_sums_t<<<c.nt, kSumThreads, 0, s>>>(c, sh.l2, lp, covered, pc.sigma2, status);
   return cudaGetLastError();
 }
 

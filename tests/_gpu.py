@@ -33,7 +33,7 @@ def run_compute(desc, x, templates, gaps=NOGAPS, mode=None, tuning=None, plan=No
     if own:
         plan = fs.Plan(desc, device=dev)
     if mode is not None or tuning:
-        plan.set_tuning(mode=mode or fs.MODE_FUSED, **(tuning or {}))
+        plan.set_tuning(mode=fs.MODE_SPLIT if mode is None else mode, **(tuning or {}))
     xd = torch.from_numpy(np.ascontiguousarray(x, np.complex64)).to(dev)
     td = fs.pack_templates(templates, device=dev)
     gd = torch.from_numpy(np.ascontiguousarray(gaps, np.int64).reshape(-1)).to(dev)
