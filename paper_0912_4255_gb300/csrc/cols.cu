@@ -28,7 +28,21 @@ cudaError_t run(const ColsArgs<R>& a, dim3 grid, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr_done = 1;
   }
-  kern<<<grid, NT, SM, s>>>(a);
+  // persistent grid: the blocks that fit on the device at once
+  static int resident = 0;
+  if (!resident) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, SM);
+    if (e != cudaSuccess) return e;
+    resident = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  // (the fused resampling source keeps one tile per block: its gathers run
+  // slower when blocks drift apart)
+  const unsigned total = grid.x * grid.y;
+  const unsigned cap = SRC == SRC_LOAD ? (unsigned)resident : total;
+  kern<<<total < cap ? total : cap, NT, SM, s>>>(a);
   return cudaGetLastError();
 }
 }  // namespace

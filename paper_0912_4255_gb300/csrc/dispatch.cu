@@ -94,7 +94,8 @@ static cudaError_t do_rows(const PlanConst& pc, const Chunk& c, const Shape& sh,
   int lc = 0;
   while ((1 << lc) < sh.cols) ++lc;
   a.log2cols = lc;
-  dim3 grid((unsigned)((1 << sh.l1) / sh.rows), ti >= 0 ? 1u : (unsigned)c.nt);
+  a.blocks_max = (1 << sh.l1) / sh.rows;
+  dim3 grid((unsigned)a.blocks_max, ti >= 0 ? 1u : (unsigned)c.nt);
   return rows_any<R>(a, sh.l2, grid, s);
 }
 

@@ -43,6 +43,7 @@ struct RowsArgs {
   int ti;
   int cols;      // C of pass A
   int log2cols;
+  int blocks_max; // row blocks of one template
 };
 
 // --------------------------------------------------------------- shapes
@@ -97,8 +98,19 @@ constexpr int blocks_for_smem(size_t bytes) { return bytes <= 110 * 1024 ? 2 : 1
 
 // --------------------------------------------------------------- pass A
 
-// One column tile of pass A for template t (all threads of the block).
-// za: this template's intermediate (a plane; the b plane follows at +N).
+// Stage twiddle tables of pass A, the same for every tile of one shape
+// (all threads of the block; read after a barrier).
+template <typename R, int L1, int C, int NT>
+__device__ __forceinline__ void cols_tables(const Tw<R>& tw, cpx<R>* buf) {
+  using PA = PlanA<L1>;
+  cpx<R>* tws = buf + 2 * C * FftGeom<L1, C>::STRIDE;
+  build_mid_tw<R, L1, 0, PA::NSL_LAST, NT>(tws, tw.tl[L1]);
+  build_stage_tw<R, L1, PA::NSL_LAST, PA::RBL, NT>(tws + PA::MID_TW, tw.tl[L1]);
+}
+
+// One column tile of pass A for template t (all threads of the block; the
+// stage tables from cols_tables).  za: this template's intermediate (a
+// plane; the b plane follows at +N).
 template <typename R, int L1, int C, int NT, int SRC, int TAPS>
 __device__ __forceinline__ void cols_tile(const ColsArgs<R>& a, int t, int tile, cpx<R>* __restrict__ buf,
                                           double* red, cpx<R>* __restrict__ za, int RRr, int lr) {
@@ -122,9 +134,9 @@ __device__ __forceinline__ void cols_tile(const ColsArgs<R>& a, int t, int tile,
     wa_in = reinterpret_cast<const Cx*>(a.c.wa) + (int64_t)t * a.c.z_stride + (int64_t)tile * (C * N1);
     wb_in = wa_in + ((int64_t)1 << L);
   }
-  // twiddle tables (read after the barriers that end the fill)
+  // twiddle tables (cols_tables); this tile's inter-pass factors are
+  // written here and read after the barriers that end the fill
   using PA = PlanA<L1>;
-  constexpr int RBL = PA::RBL;
   constexpr int NSL_LAST = PA::NSL_LAST;
   constexpr int RADL = PA::RADL;
   constexpr int NS = PA::NS;
@@ -132,8 +144,6 @@ __device__ __forceinline__ void cols_tile(const ColsArgs<R>& a, int t, int tile,
   cpx<R>* tlast = tws + PA::MID_TW;       // last stage, [q - 1][j]
   cpx<R>* ta = tlast + PA::LAST_TW;       // [c][j]: W_N^{j (c0 + c)}, j < NS
   cpx<R>* tb = ta + C * NS;               // [c][q]: W_N^{q NS (c0 + c)}, q < RADL
-  build_mid_tw<R, L1, 0, NSL_LAST, NT>(tws, a.tw.tl[L1]);
-  build_stage_tw<R, L1, NSL_LAST, RBL, NT>(tlast, a.tw.tl[L1]);
   for (int e = threadIdx.x; e < C * (NS + RADL); e += NT) {
     if (e < C * NS) {
       const int c = e / NS, j = e - c * NS;
@@ -144,27 +154,48 @@ __device__ __forceinline__ void cols_tile(const ColsArgs<R>& a, int t, int tile,
       tb[e2] = twiddle<R>(a.tw, L, (uint32_t)(q * NS) * (uint32_t)(c0 + c));
     }
   }
-  GapCursor gc = make_cursor(m, a.gaps);
+  if constexpr (SRC == SRC_LOAD) {
+    // first radix-16 stage straight from the resampled series: unit
+    // (series, j, column) with the column fastest, so that the lanes of a
+    // warp read consecutive values; outputs in the order of a first
+    // Stockham stage (sub-transforms of length 16 at 16 j)
+    constexpr int Q1 = N1 / 16;
+#pragma unroll 1
+    for (int u = threadIdx.x; u < 2 * C * Q1; u += NT) {
+      const int c = u & (C - 1);
+      const int rest = u / C;
+      const int j = rest & (Q1 - 1);
+      const int sr = rest / Q1;
+      const Cx* src = (sr ? wb_in : wa_in) + c;
+      Cx v[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const int k1 = j + r * Q1;
+        v[r] = c0 + c + k1 * N2 < n_b ? __ldcs(src + k1 * C) : czero<Cx>();
+      }
+      Dft<Cx, 16>::run(v);
+      Cx* dst = buf + (sr * C + c) * STRIDE;
+#pragma unroll
+      for (int r = 0; r < 16; ++r) dst[pidx(16 * j + r)] = v[r];
+    }
+  } else {
+    GapCursor gc = make_cursor(m, a.gaps);
 #pragma unroll 2
-  for (int i = threadIdx.x; i < C * N1; i += NT) {
-    const int c = i & (C - 1);
-    const int k1 = i / C;
-    const int k = c0 + c + k1 * N2;
-    Cx va = czero<Cx>(), vb = czero<Cx>();
-    if (k < n_b) {
-      if constexpr (SRC == SRC_LOAD) {
-        va = __ldcs(wa_in + i);
-        vb = __ldcs(wb_in + i);
-      } else {
+    for (int i = threadIdx.x; i < C * N1; i += NT) {
+      const int c = i & (C - 1);
+      const int k1 = i / C;
+      const int k = c0 + c + k1 * N2;
+      Cx va = czero<Cx>(), vb = czero<Cx>();
+      if (k < n_b) {
         R aa, bb;
         if (sample_weights<R, SRC == SRC_NN ? FSTAT_NEAREST : FSTAT_SINC, TAPS>(a.pc, kn, k, a.x, gc, a.wcs,
                                                                               va, vb, aa, bb)) {
           pA += aa * aa; pB += bb * bb; pC += aa * bb;
         }
       }
+      buf[c * STRIDE + pidx(k1)] = va;
+      buf[(C + c) * STRIDE + pidx(k1)] = vb;
     }
-    buf[c * STRIDE + pidx(k1)] = va;
-    buf[(C + c) * STRIDE + pidx(k1)] = vb;
   }
   if constexpr (SRC != SRC_LOAD) {
     double sA, sB, sC;
@@ -176,8 +207,10 @@ __device__ __forceinline__ void cols_tile(const ColsArgs<R>& a, int t, int tile,
     finalize_sums(a.c.meta + t, part, tiles, a.c.counters + t, a.pc.sigma2, nullptr, a.status);
   }
   __syncthreads();
-  // all stages but the last in shared memory
-  fft_mid_stages<R, L1, 0, NSL_LAST, NT, 2 * C, STRIDE>(buf, tws);
+  // all stages but the last in shared memory (the first one done above when
+  // loading; it needs no twiddles, so the tables start at the same place)
+  static_assert(stage_tw_count<0, 4>() == 0, "first stage without twiddles");
+  fft_mid_stages<R, L1, SRC == SRC_LOAD ? 4 : 0, NSL_LAST, NT, 2 * C, STRIDE>(buf, tws);
   // last stage: inputs from shared memory, outputs X[p1 = j + q NS] stay in
   // registers, are multiplied by W_N^{p1 k2} and stored into Z.  Lanes run
   // over j mod RR, then the column, then j / RR, so that a warp writes runs
@@ -211,22 +244,42 @@ __device__ __forceinline__ void cols_tile(const ColsArgs<R>& a, int t, int tile,
   }
 }
 
+// Persistent over the (template, column tile) items of a chunk: the grid is
+// sized to the resident blocks, each builds the stage tables once.
 template <typename R, int L1, int C, int NT, int SRC, int TAPS>
 __global__ void __launch_bounds__(NT, (blocks_for_smem(cols_smem<R, L1, C>()))) k_cols(ColsArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[96];
-  const int t = a.ti >= 0 ? a.ti : (int)blockIdx.y;
-  const TmplMeta& m = a.c.meta[t];
-  const int tiles = (1 << (m.log2n - L1)) / C;
-  if ((int)blockIdx.x >= tiles || m.status != FSTAT_OK) return;
-  cpx<R>* za = reinterpret_cast<cpx<R>*>(a.c.za) + (int64_t)t * a.c.z_stride;
-  cols_tile<R, L1, C, NT, SRC, TAPS>(a, t, blockIdx.x, reinterpret_cast<cpx<R>*>(smem_raw), red, za, a.rr,
-                                     a.log2rr);
+  cpx<R>* buf = reinterpret_cast<cpx<R>*>(smem_raw);
+  cols_tables<R, L1, C, NT>(a.tw, buf);
+  const int nt = a.ti >= 0 ? 1 : a.c.nt;
+  const int total = a.tiles_max * nt;
+#pragma unroll 1
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const int tq = w / a.tiles_max;
+    const int tile = w - tq * a.tiles_max;
+    const int t = a.ti >= 0 ? a.ti : tq;
+    const TmplMeta& m = a.c.meta[t];
+    if (tile >= (1 << (m.log2n - L1)) / C || m.status != FSTAT_OK) continue;
+    cpx<R>* za = reinterpret_cast<cpx<R>*>(a.c.za) + (int64_t)t * a.c.z_stride;
+    cols_tile<R, L1, C, NT, SRC, TAPS>(a, t, tile, buf, red, za, a.rr, a.log2rr);
+    __syncthreads();                      // the next tile reuses buf and its twiddle factors
+  }
 }
 
 // --------------------------------------------------------------- pass B
 
-// One row block of pass B for template t; za: the template's intermediate.
+// Stage twiddle tables of pass B (all threads of the block; read after a barrier).
+template <typename R, int L2, int RR, int NT>
+__device__ __forceinline__ void rows_tables(const Tw<R>& tw, cpx<R>* buf) {
+  using PB = PlanB<L2>;
+  cpx<R>* tws = buf + 2 * RR * FftGeom<L2, RR>::STRIDE;
+  build_mid_tw<R, L2, PB::RB0, PB::NSL_LAST, NT>(tws, tw.tl[L2]);
+  build_stage_tw<R, L2, PB::NSL_LAST, PB::RBL, NT>(tws + PB::MID_TW, tw.tl[L2]);
+}
+
+// One row block of pass B for template t (stage tables from rows_tables);
+// za: the template's intermediate.
 template <typename R, int L2, int RR, int NT>
 __device__ __forceinline__ void rows_tile(const RowsArgs<R>& a, int t, int blk, cpx<R>* __restrict__ buf,
                                           const cpx<R>* __restrict__ zbase) {
@@ -251,10 +304,8 @@ __device__ __forceinline__ void rows_tile(const RowsArgs<R>& a, int t, int blk, 
   const Cx* za = zbase + (int64_t)blk * N2 * RR;
   const Cx* zb = za + ((int64_t)1 << L);
   using PB = PlanB<L2>;
-  Cx* tws = buf + 2 * RR * STRIDE;        // shared-memory stages
+  Cx* tws = buf + 2 * RR * STRIDE;        // shared-memory stages (rows_tables)
   Cx* tlast = tws + PB::MID_TW;           // last stage, [q - 1][j]
-  build_mid_tw<R, L2, PB::RB0, PB::NSL_LAST, NT>(tws, a.tw.tl[L2]);
-  build_stage_tw<R, L2, PB::NSL_LAST, PB::RBL, NT>(tlast, a.tw.tl[L2]);
   constexpr int RB0 = PB::RB0;
   constexpr int RAD0 = 1 << RB0;
   constexpr int Q0 = N2 / RAD0;                   // butterflies per sequence
@@ -318,14 +369,26 @@ __device__ __forceinline__ void rows_tile(const RowsArgs<R>& a, int t, int blk, 
   }
 }
 
+// Persistent over the (template, row block) items of a chunk.
 template <typename R, int L2, int RR, int NT>
 __global__ void __launch_bounds__(NT, (blocks_for_smem(rows_smem<R, L2, RR>()))) k_rows(RowsArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int t = a.ti >= 0 ? a.ti : (int)blockIdx.y;
-  const TmplMeta& m = a.c.meta[t];
-  if ((int)blockIdx.x * RR >= (1 << (m.log2n - L2))) return;
-  const cpx<R>* za = reinterpret_cast<const cpx<R>*>(a.c.za) + (int64_t)t * a.c.z_stride;
-  rows_tile<R, L2, RR, NT>(a, t, blockIdx.x, reinterpret_cast<cpx<R>*>(smem_raw), za);
+  cpx<R>* buf = reinterpret_cast<cpx<R>*>(smem_raw);
+  rows_tables<R, L2, RR, NT>(a.tw, buf);
+  __syncthreads();
+  const int nt = a.ti >= 0 ? 1 : a.c.nt;
+  const int total = a.blocks_max * nt;
+#pragma unroll 1
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const int tq = w / a.blocks_max;
+    const int blk = w - tq * a.blocks_max;
+    const int t = a.ti >= 0 ? a.ti : tq;
+    const TmplMeta& m = a.c.meta[t];
+    if (blk * RR >= (1 << (m.log2n - L2))) continue;
+    const cpx<R>* za = reinterpret_cast<const cpx<R>*>(a.c.za) + (int64_t)t * a.c.z_stride;
+    rows_tile<R, L2, RR, NT>(a, t, blk, buf, za);
+    __syncthreads();                      // the next block reuses buf
+  }
 }
 
 }  // namespace fs

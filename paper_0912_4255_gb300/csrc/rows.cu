@@ -27,7 +27,18 @@ cudaError_t FS_CAT(rows, FS_REAL, FS_L2)(const RowsArgs<FS_REAL>& a, dim3 grid, 
     if (e != cudaSuccess) return e;
     attr_done = 1;
   }
-  kern<<<grid, NT, SM, s>>>(a);
+  // persistent grid: the blocks that fit on the device at once
+  static int resident = 0;
+  if (!resident) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, SM);
+    if (e != cudaSuccess) return e;
+    resident = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  const unsigned total = grid.x * grid.y;
+  kern<<<total < (unsigned)resident ? total : (unsigned)resident, NT, SM, s>>>(a);
   return cudaGetLastError();
 }
 int FS_CAT(rowsR, FS_REAL, FS_L2)() { return cols_for<FS_REAL>(FS_L2); }

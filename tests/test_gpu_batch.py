@@ -8,7 +8,7 @@ import synth
 from oracle import fstat as F
 from oracle import resample as R
 
-from _gpu import injected_series, r15, run_compute
+from _gpu import MODES, injected_series, r15, run_compute
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-4
@@ -66,7 +66,7 @@ def test_persistent_equals_fused_and_graph_replay():
     x, _ = injected_series(desc, 71, [synth.random_injection(72, df=0.2)], gaps)
     a, d = synth.fibonacci_sky(7)
     tm = synth.make_templates(a, d, np.linspace(-2e-9, 0, 7), 0, desc.n_data, 0, len(gaps))
-    ref, rc = run_compute(desc, x, tm, gaps)
+    ref, rc = run_compute(desc, x, tm, gaps, mode=MODES["fused"])
     assert rc == 0
     dev = torch.device("cuda:0")
     plan = fs.Plan(desc)
@@ -77,6 +77,38 @@ def test_persistent_equals_fused_and_graph_replay():
     eager = fs.fstat_compute(plan, xd, td, gd).cpu().numpy().reshape(len(tm), -1)
     assert fs.fstat_status(plan, raise_error=False) == 0
     assert r15(eager, ref) < 1e-6
+    runner = fs.GraphRunner(plan, xd, td, gd)
+    runner.twoF.fill_(0)
+    for _ in range(2):
+        got = runner.replay()
+    torch.cuda.synchronize()
+    assert fs.fstat_status(plan, raise_error=False) == 0
+    assert np.array_equal(got.cpu().numpy().reshape(len(tm), -1), eager)
+
+
+def test_split_graph_replay_matches_eager():
+    """The default (split) mode captured in a CUDA graph: the resampler, the
+    A/B/C reduction and both passes replay bit for bit, and agree with the
+    fused mode to rounding of the sums."""
+    import torch
+    import paper_0912_4255_gb300 as fs
+    desc = synth.PlanDesc(dt=0.5, n_data=100_000, n_fft=1 << 17, interp=R.SINC, f_het=90.0,
+                          max_templates=7)
+    gaps = synth.gap_intervals(desc.n_data, 0.1, 3600, 9000, seed=6)
+    x, _ = injected_series(desc, 73, [synth.random_injection(74, df=-0.2)], gaps)
+    a, d = synth.fibonacci_sky(7)
+    tm = synth.make_templates(a, d, np.linspace(-2e-9, 0, 7), 0, desc.n_data, 0, len(gaps))
+    fused, rc = run_compute(desc, x, tm, gaps, mode=MODES["fused"])
+    assert rc == 0
+    dev = torch.device("cuda:0")
+    plan = fs.Plan(desc)
+    assert plan.tuning()["mode"] == fs.MODE_SPLIT
+    xd = torch.from_numpy(x).to(dev)
+    td = fs.pack_templates(tm, device=dev)
+    gd = torch.from_numpy(gaps.reshape(-1).copy()).to(dev)
+    eager = fs.fstat_compute(plan, xd, td, gd).cpu().numpy().reshape(len(tm), -1)
+    assert fs.fstat_status(plan, raise_error=False) == 0
+    assert r15(eager, fused) < 1e-5
     runner = fs.GraphRunner(plan, xd, td, gd)
     runner.twoF.fill_(0)
     for _ in range(2):
@@ -105,5 +137,5 @@ def test_persistent_bounded_wait_reports_timeout_and_recovers():
     assert fs.fstat_status(plan, raise_error=False) == fs._lib.FSTAT_ETIMEOUT
     good = fs.fstat_compute(plan, xd, td).cpu().numpy().reshape(4, -1)
     assert fs.fstat_status(plan, raise_error=False) == 0
-    ref, _ = run_compute(desc, x, tm)
+    ref, _ = run_compute(desc, x, tm, mode=MODES["fused"])
     assert r15(good, ref) < 1e-6

@@ -148,6 +148,32 @@ def test_host_grid_length_matches_oracle():
         assert nb[i] == TM.grid(tm[i], d)[1]
 
 
+def test_grid_length_within_velocity_bound():
+    """The tiled resampler's grid is sized from n_b <= (n_data - 1)(1 + beta)
+    + 1 with beta = (2 pi/year) AU/c + (2 pi/sidereal day) R/c, the largest
+    |dt_m/dt| of the analytic ephemeris (Eq. 4pt2).  The host n_b of sky
+    positions all over the sphere, those in the ecliptic and at the extremes
+    of the orbital Doppler included, stays within it."""
+    import paper_0912_4255_gb300 as fs
+    d = synth.search_plan(max_templates=16)
+    c = 299792458.0
+    beta = 2 * np.pi / d.eph.year_s * d.eph.au_m / c + 2 * np.pi / d.eph.sidereal_day_s * d.det.radius_m / c
+    bound = (d.n_data - 1) * (1 + beta) + 1
+    plan = fs.Plan(d)
+    eps = d.eph.obliquity_rad
+    lam = np.linspace(0, 2 * np.pi, 64, endpoint=False)
+    # ecliptic longitudes -> equatorial (alpha, delta) on the ecliptic
+    al = np.arctan2(np.sin(lam) * np.cos(eps), np.cos(lam)) % (2 * np.pi)
+    de = np.arcsin(np.sin(lam) * np.sin(eps))
+    a2, d2 = synth.fibonacci_sky(192)
+    al = np.concatenate([al, a2]); de = np.concatenate([de, d2])
+    tm = synth.make_templates(al, de, 0.0, 0, d.n_data)
+    nb = fs.fstat_template_nb(plan, tm)
+    assert nb.max() <= bound
+    # the Doppler of the orbit moves the bound: some position gets close to it
+    assert nb.max() > (d.n_data - 1) * (1 + 0.5 * beta)
+
+
 def test_search_size_full_bins():
     """Search-sized workload (10 d, 1,728,000 samples, FFT 2^22, 10 % gaps,
     8-tap sinc) in the launch configuration the benchmark times: every bin
