@@ -729,7 +729,7 @@ __device__ __forceinline__ void stockham_stage(cpx<R>* __restrict__ buf, const c
       const C* src = buf + f * STRIDE;
 #pragma unroll
       for (int bb = 0; bb < BPU; ++bb) {
-        const int j = w * BPU + bb;
+        const int j = w + bb * UNITS_PER_SEQ;     // lanes take consecutive butterflies
         const int k = j & (NS - 1);
 #pragma unroll
         for (int r = 0; r < RAD; ++r) v[u][bb * RAD + r] = src[pidx(j + r * (N / RAD))];
@@ -751,7 +751,7 @@ __device__ __forceinline__ void stockham_stage(cpx<R>* __restrict__ buf, const c
       C* dst = buf + f * STRIDE;
 #pragma unroll
       for (int bb = 0; bb < BPU; ++bb) {
-        const int j = w * BPU + bb;
+        const int j = w + bb * UNITS_PER_SEQ;
         const int k = j & (NS - 1);
         const int base = ((j >> NSL) << (NSL + RB)) + k;
 #pragma unroll
