@@ -149,20 +149,23 @@ def fp32_peak_tflops(sm_mhz: float) -> float:
 
 
 def algorithmic_per_template(desc, fused=True):
-    """(FLOPs, bytes) of one template in each kernel, counted from the
-    algorithm (not from the implementation):
-    * FFTs: 5 N log2 N per complex transform of length N, two series (F_a, F_b);
-      the first pass does the log2 N1 part, the second the log2 N2 part;
-    * inter-pass twiddle: one complex multiply per element and series (6 flop);
+    """(FLOPs, design bytes) of one template in each kernel.
+
+    FLOPs, counted from the algorithm:
+    * FFTs: 5 N log2 N per complex transform of length N, two series (F_a,
+      F_b); the first pass does the log2 N1 part, the second the log2 N2 part;
+      the inter-pass twiddle is one complex multiply per element and series;
     * resampling, per grid point: K taps x (4 flop complex MAC + 5 flop
       weight) + 16 flop (phase rotation, a/b weights, sums A, B, C);
-    * 2F: 12 flop per bin;
-    * time map: 80-byte knot record per 2^log2h grid points (FP64 work);
-    * bytes: x_h read once (8 B/sample) by the resampling, 2F written (4 B/bin)
-      in the second pass.
-    Unfused (split) execution moves the resampling FLOPs and the x_h read out
-    of the first pass into the resample kernel, and adds the resampled series
-    (two complex64 per grid point below n_b), written once and read once."""
+    * 2F: 12 flop per bin.
+    Design bytes, the HBM traffic the four-step design needs (N_d data
+    samples ~ N_b grid points, N = n_fft):
+    * time map: an 80-byte knot record per 2^10 grid points;
+    * resample (split): read x_h 8 N_d, write w_a, w_b 16 N_b;
+    * first pass: read w_a, w_b 16 N_b (split) or x_h 8 N_d (fused), write the
+      intermediate 16 N;
+    * second pass: read the intermediate 16 N, write 2F 4 N.
+    The path's own algorithmic bytes are 8 N_d + 4 N (path_bytes)."""
     n = int(desc.n_fft)
     L = int(math.log2(n))
     l1 = min(12, (L + 1) // 2)
@@ -170,18 +173,23 @@ def algorithmic_per_template(desc, fused=True):
         l1 = L - 12
     l2 = L - l1
     taps = desc.taps if desc.interp == 1 else 1
-    nb = desc.n_data
+    nd = float(desc.n_data)
     fft_a = 2 * 5 * n * l1 + 2 * 6 * n
-    res = nb * (taps * 9 + 16)
+    res = nd * (taps * 9 + 16)
     rows = 2 * 5 * n * l2 + 12 * n
-    out = {"fft_rows": (rows, 4.0 * n), "timemap": (0.0, 80.0 * (n >> 10)), "sums": (0.0, 0.0),
-           "persistent": (fft_a + res + rows, 8.0 * desc.n_data + 4.0 * n)}
+    out = {"fft_rows": (rows, 16.0 * n + 4.0 * n), "timemap": (0.0, 80.0 * (n >> 10)), "sums": (0.0, 0.0),
+           "persistent": (fft_a + res + rows, 8.0 * nd + 32.0 * n + 4.0 * n)}
     if fused:
-        out["fft_cols"] = (fft_a + res, 8.0 * desc.n_data)
+        out["fft_cols"] = (fft_a + res, 8.0 * nd + 16.0 * n)
     else:
-        out["resample"] = (res, 8.0 * desc.n_data + 16.0 * nb)
-        out["fft_cols"] = (fft_a, 16.0 * nb)
+        out["resample"] = (res, 8.0 * nd + 16.0 * nd)
+        out["fft_cols"] = (fft_a, 16.0 * nd + 16.0 * n)
     return out
+
+
+def path_bytes(desc):
+    """Algorithmic bytes of the whole path per template: read x_h once, write 2F."""
+    return 8.0 * desc.n_data + 4.0 * desc.n_fft
 
 
 def ncu_traffic(kernel: str, templates_per_launch: float):
@@ -357,10 +365,14 @@ def main():
         kernels[k] = {"launches": int(k_n), "ms_per_launch": k_ms / k_n,
                       "templates_per_launch": tpl_per_launch,
                       "tflops": flops * tpl_per_launch / t_launch / 1e12,
-                      "alg_gbs": nbytes * tpl_per_launch / t_launch / 1e9}
+                      "design_bytes_per_launch": nbytes * tpl_per_launch,
+                      "design_gbs": nbytes * tpl_per_launch / t_launch / 1e9}
     dom = max(kernels, key=lambda k: prof[k][0])
     kd = kernels[dom]
     traffic = ncu_traffic(dom, kd["templates_per_launch"])
+    # whole path: algorithmic and design bytes per template at the measured rate
+    tpl_per_s = n_t * world / (ms_per_step / 1e3)
+    design_tpl = sum(per_tpl[k][1] for k in kernels if k in per_tpl)
     launches = sum(v[1] for v in prof.values())
     kernel_ms = {k: round(v[0] / args.steps, 3) for k, v in prof.items() if v[1]}
     # ---- end to end through the public API: pinned host in, pinned host out
@@ -376,12 +388,21 @@ def main():
         "data": "synthetic (seeded complex Gaussian noise with gaps; analytic ephemeris)",
         "config": config_dict(desc, n_t, world),
         "kernel_ms_per_step": kernel_ms,
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": kd["tflops"], "peak": peak_tf,
-                     "unit": "TFLOP/s", "frac": kd["tflops"] / peak_tf,
-                     "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock under load)",
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": kd["design_gbs"], "peak": peak_gbs,
+                     "unit": "GB/s", "frac": kd["design_gbs"] / peak_gbs,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                     "bytes": "design bytes of the four-step path per launch (see algorithmic_per_template)",
+                     "bytes_per_launch": kd["design_bytes_per_launch"],
                      "traffic": traffic,
-                     "hbm": {"alg_gbs": kd["alg_gbs"], "peak": peak_gbs, "frac": kd["alg_gbs"] / peak_gbs,
-                             "peak_source": peak_kind}},
+                     "alu": {"achieved": kd["tflops"], "peak": peak_tf, "unit": "TFLOP/s",
+                             "frac": kd["tflops"] / peak_tf,
+                             "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz"}},
+        "path": {"alg_bytes_per_template": path_bytes(desc),
+                 "alg_gbs": path_bytes(desc) * tpl_per_s / 1e9,
+                 "alg_frac": path_bytes(desc) * tpl_per_s / 1e9 / peak_gbs,
+                 "design_bytes_per_template": design_tpl,
+                 "design_gbs": design_tpl * tpl_per_s / 1e9,
+                 "design_frac": design_tpl * tpl_per_s / 1e9 / peak_gbs},
         "kernels": kernels,
         "clocks": clocks, "gpu_launches": int(launches), "tuning": plan.tuning(),
     }

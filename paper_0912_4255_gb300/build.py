@@ -51,7 +51,7 @@ def _sources_digest() -> str:
         fp = p if os.path.isabs(p) else os.path.join(CSRC, p)
         if os.path.isfile(fp):
             with open(fp, "rb") as f:
-                h.update(fp.encode())
+                h.update(os.path.relpath(fp, os.path.dirname(HERE)).encode())   # same on every machine
                 h.update(f.read())
     h.update(" ".join(ARCH + FLAGS).encode())
     return h.hexdigest()
