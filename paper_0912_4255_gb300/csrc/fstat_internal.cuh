@@ -38,6 +38,7 @@ struct PlanConst {
   double auc, rc;                                 // AU/c, R/c (s)
   double wo, ws;                                  // orbital and sidereal rates (rad/s)
   double th0;                                     // sidereal angle of the meridian at t = 0
+  double inv_dt;                                  // 1 / dt
 };
 
 // Per-template state produced by the time-map kernel and completed by the
@@ -211,26 +212,66 @@ __device__ __forceinline__ void beams(const PlanConst& pc, const Sky<R>& s, R t,
   beams_h<R>(pc, s, sH, cH, a, b, da, db);
 }
 
-// Detector time T with T + t_m(T) = tb (Eq. 21), by Newton's method started
-// from tb - t_m(tb); |dt_m/dt| <~ 1e-4 and |d2t_m/dt2| <~ 1e-10 s^-1 make
-// two steps exact to rounding.  Returns t_m(T), its rate and the hour-angle
-// sine/cosine at T (from the last evaluation, corrected to first order).
+// sin and cos of a small angle x (|x| <= 0.1) by their Taylor series to x^13
+// and x^12 (truncation below 1e-19 relative).
+template <typename R>
+__device__ __forceinline__ void sincos_small(R x, R* s, R* c) {
+  const R x2 = x * x;
+  // coefficients 1/((2k)(2k+1)) and 1/((2k-1)(2k)) as compile-time constants
+  *s = x * (1 - x2 * (R)(1.0 / 6) * (1 - x2 * (R)(1.0 / 20) * (1 - x2 * (R)(1.0 / 42) * (1 - x2 * (R)(1.0 / 72) *
+       (1 - x2 * (R)(1.0 / 110) * (1 - x2 * (R)(1.0 / 156)))))));
+  *c = 1 - x2 * (R)0.5 * (1 - x2 * (R)(1.0 / 12) * (1 - x2 * (R)(1.0 / 30) * (1 - x2 * (R)(1.0 / 56) *
+       (1 - x2 * (R)(1.0 / 90) * (1 - x2 * (R)(1.0 / 132))))));
+}
+
+// (sin, cos) of an angle advanced by d: rotate (s, c) by d, d small when
+// possible, else a full evaluation of the advanced angle a + d.
+template <typename R>
+__device__ __forceinline__ void advance(R a, R d, R* s, R* c) {
+  if (fabs(d) <= (R)0.1) {
+    R sd, cd;
+    sincos_small<R>(d, &sd, &cd);
+    const R s0 = *s, c0 = *c;
+    *s = s0 * cd + c0 * sd;
+    *c = c0 * cd - s0 * sd;
+  } else {
+    rsincos<R>(a + d, s, c);
+  }
+}
+
+// Detector time T with T + t_m(T) = tb (Eq. 21), by one Newton step from
+// T0 = tb - t_m(tb): |dt_m/dt| <~ 1e-4 puts T0 within ~5e-2 s of T and
+// |d2t_m/dt2| <~ 1e-10 s^-1 leaves ~1e-13 s after the step, below the
+// rounding of T.  The orbital phase and hour angle at T0 and T are those at
+// tb rotated by small angles (|t_m| <= AU/c + R/c), so only tb needs full
+// sines and cosines.  Returns t_m(T), its rate and the hour-angle
+// sine/cosine at T, and 1 / (1 + dt_m/dt).
 template <typename R>
 __device__ __forceinline__ R inverse_time(const PlanConst& pc, const Sky<R>& s, R tb,
-                                          R* tm_out, R* rate_out, R* sH, R* cH) {
-  R tm, rate;
-  roemer<R>(pc, s, tb, &tm, &rate);
-  R T = tb - tm;
-  R dT = 0;
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    roemer<R>(pc, s, T, &tm, &rate, sH, cH);
-    dT = -(T + tm - tb) / (1 + rate);
-    T += dT;
-  }
+                                          R* tm_out, R* rate_out, R* sH, R* cH, R* inv1r_out) {
+  const R wo = (R)pc.wo, ws = (R)pc.ws;
+  const R phi = (R)pc.orb0 + wo * tb, hh = (R)pc.th0 + ws * tb - s.alpha;
+  R sp, cp, st, ct;
+  rsincos<R>(phi, &sp, &cp);
+  rsincos<R>(hh, &st, &ct);
+  R tm = s.ox * cp + s.oy * sp + s.rxy * ct + s.rz;
+  // T0 = tb - tm: phases move by -w tm
+  const R d0 = -tm;
+  advance<R>(phi, wo * d0, &sp, &cp);
+  advance<R>(hh, ws * d0, &st, &ct);
+  const R T0 = tb + d0;
+  tm = s.ox * cp + s.oy * sp + s.rxy * ct + s.rz;
+  const R rate = wo * (s.oy * cp - s.ox * sp) - ws * s.rxy * st;
+  const R inv1r = 1 / (1 + rate);
+  const R dT = -(T0 + tm - tb) * inv1r;
+  *inv1r_out = inv1r;
+  // the hour angle at T to first order in ws dT (|ws dT| <~ 4e-6)
+  const R e = ws * dT;
+  *sH = st + ct * e;
+  *cH = ct - st * e;
   *tm_out = tm + rate * dT;
   *rate_out = rate;
-  return T;
+  return T0 + dT;
 }
 
 // ---------------------------------------------------------------- samples
@@ -356,6 +397,31 @@ __device__ __forceinline__ float rcp_approx(float v) {
 // K(x) = 4 sin(pi x) sin(pi x/4) / (pi^2 x^2); plain truncation: sin(pi x)/(pi x).
 // The common factor s leaves the sum over taps.  Returns the mask (the
 // nearest sample is valid data); taps on invalid samples weigh zero.
+// The taps of a window that touches a gap or the span's edge: each tap on
+// an invalid sample weighs zero; the result is valid when the nearest sample
+// is.  w0..w3: the window factors of taps 0..3 (sinc8_f32).
+__device__ __forceinline__ bool sinc8_f32_edge(const float2* __restrict__ x, GapCursor& gc, bool lanczos,
+                                            int jlo, int jnn, float f, float w0, float w1, float w2,
+                                            float w3, float2& acc) {
+  bool msk = false;
+  acc = make_float2(0.f, 0.f);
+  for (int i = 0; i < 8; ++i) {
+    const int j = jlo + i;
+    const bool ok = gc.valid(j);
+    if (j == jnn) msk = ok;
+    if (!ok) continue;
+    const float2 t = __ldg(x + j);
+    const float xi = f + (float)(3 - i);
+    const float sg = ((3 - i) & 1) ? -1.0f : 1.0f;              // (-1)^(3-i)
+    const int q = i & 3;
+    const float wq = q == 0 ? w0 : (q == 1 ? w1 : (q == 2 ? w2 : w3));
+    const float w = lanczos ? sg * (i < 4 ? wq : -wq) * rcp_approx(xi * xi) : sg * rcp_approx(xi);
+    acc.x = fmaf(w, t.x, acc.x);
+    acc.y = fmaf(w, t.y, acc.y);
+  }
+  return msk;
+}
+
 __device__ __forceinline__ bool sinc8_f32(const float2* __restrict__ x, GapCursor& gc, bool lanczos,
                                           int n0, int qoff, float f, float dn, float2& z) {
   const int jlo = n0 - 3;
@@ -371,13 +437,6 @@ __device__ __forceinline__ bool sinc8_f32(const float2* __restrict__ x, GapCurso
   if (full) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = __ldg(x + jlo + i);
-  } else {
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      int j = jlo + i;
-      j = j < gc.lo ? gc.lo : (j >= gc.hi ? gc.hi - 1 : j);
-      v[i] = __ldg(x + j);
-    }
   }
   // sin, cos of pi dn / 4 by the polynomial; sin(pi dn) by two doublings
   float sh, ch;
@@ -385,36 +444,43 @@ __device__ __forceinline__ bool sinc8_f32(const float2* __restrict__ x, GapCurso
   const float s2 = 2.0f * sh * ch, c2 = fmaf(ch, ch, -sh * sh);
   const float sdn = 2.0f * s2 * c2;
   const float sf = qoff ? -sdn : sdn;                     // sin(pi f)
-  float g[8];
+  float2 acc = make_float2(0.f, 0.f);
+  // sin(pi x_i / 4) for i = 0..3: with p = (sin + cos)(pi dn/4) / sqrt 2 and
+  // m = (cos - sin)(pi dn/4) / sqrt 2 these are (m, cos, p, sin) for
+  // qoff = 0 and (-sin, m, cos, p) for qoff = 1 (f/4 = dn/4 + 1/4)
+  const float r2 = 0.70710678118654752f;
+  const float p = (sh + ch) * r2, m = (ch - sh) * r2;
+  const float w0 = qoff ? -sh : m, w1 = qoff ? m : ch, w2 = qoff ? ch : p, w3 = qoff ? p : sh;
   if (lanczos) {
-    // sin(pi x_i / 4) for i = 0..3: with p = (sin + cos)(pi dn/4) / sqrt 2 and
-    // m = (cos - sin)(pi dn/4) / sqrt 2 these are (m, cos, p, sin) for
-    // qoff = 0 and (-sin, m, cos, p) for qoff = 1 (f/4 = dn/4 + 1/4)
-    const float r2 = 0.70710678118654752f;
-    const float p = (sh + ch) * r2, m = (ch - sh) * r2;
-    const float w0 = qoff ? -sh : m, w1 = qoff ? m : ch, w2 = qoff ? ch : p, w3 = qoff ? p : sh;
     // sign (-1)^(3-i) times the window, i = 0..3; taps 4..7 take the negatives
+    float g[8];
     g[0] = -w0; g[1] = w1; g[2] = -w2; g[3] = w3;
     g[4] = w0; g[5] = -w1; g[6] = w2; g[7] = -w3;
-  } else {
+    if (full) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) g[i] = ((3 - i) & 1) ? -1.0f : 1.0f;
-  }
-  float2 acc = make_float2(0.f, 0.f);
-  bool msk = full;
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const float xi = f + (float)(3 - i);
-    float w = lanczos ? g[i] * rcp_approx(xi * xi) : g[i] * rcp_approx(xi);
-    if (!full) {
-      const bool ok = gc.valid(jlo + i);
-      if (jlo + i == jnn) msk = ok;
-      if (!ok) w = 0.0f;
+      for (int i = 0; i < 8; ++i) {
+        const float xi = f + (float)(3 - i);
+        const float w = g[i] * rcp_approx(xi * xi);
+        acc.x = fmaf(w, v[i].x, acc.x);
+        acc.y = fmaf(w, v[i].y, acc.y);
+      }
     }
-    acc.x = fmaf(w, v[i].x, acc.x);
-    acc.y = fmaf(w, v[i].y, acc.y);
+  } else {
+    if (full) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float w = rcp_approx(f + (float)(3 - i));
+        if ((3 - i) & 1) {
+          acc.x = fmaf(-w, v[i].x, acc.x);
+          acc.y = fmaf(-w, v[i].y, acc.y);
+        } else {
+          acc.x = fmaf(w, v[i].x, acc.x);
+          acc.y = fmaf(w, v[i].y, acc.y);
+        }
+      }
+    }
   }
-  if (!msk) return false;
+  if (!full && !sinc8_f32_edge(x, gc, lanczos, jlo, jnn, f, w0, w1, w2, w3, acc)) return false;
   const float sc = lanczos ? sf * (float)(4.0 / (3.14159265358979323846 * 3.14159265358979323846))
                            : sf * (float)(1.0 / 3.14159265358979323846);
   z = make_float2(acc.x * sc, acc.y * sc);
@@ -903,6 +969,7 @@ inline void derive_constants(PlanConst& pc) {
   pc.auc = pc.au / kC; pc.rc = pc.radius / kC;
   pc.wo = kTwoPi / pc.year; pc.ws = kTwoPi / pc.sid;
   pc.th0 = pc.sid0 + pc.lon;
+  pc.inv_dt = 1.0 / pc.dt;
 }
 
 // Host copy of the t_b-grid computation (same formulas, FP64) used to size

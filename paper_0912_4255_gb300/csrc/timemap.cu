@@ -29,11 +29,11 @@ template <typename R>
 __device__ KnotVal<R> knot_value(const PlanConst& pc, const Sky<R>& sky, double tb0, int64_t k, R fdot) {
   KnotVal<R> v;
   const R tb = (R)(tb0 + (double)k * pc.dt);
-  R tm, rate, sH, cH;
-  const R T = inverse_time<R>(pc, sky, tb, &tm, &rate, &sH, &cH);
-  const R dTdk = (R)pc.dt / (1 + rate);
-  v.U = (T - (R)pc.t_start) / (R)pc.dt;
-  v.dU = 1 / (1 + rate);
+  R tm, rate, sH, cH, inv1r;
+  const R T = inverse_time<R>(pc, sky, tb, &tm, &rate, &sH, &cH, &inv1r);
+  const R dTdk = (R)pc.dt * inv1r;
+  v.U = (T - (R)pc.t_start) * (R)pc.inv_dt;
+  v.dU = inv1r;
   const R taub = tb - (R)pc.t_start;
   v.P = (R)pc.f_het * tm + (R)0.5 * fdot * taub * taub;
   v.dP = (R)pc.f_het * rate * dTdk + fdot * taub * (R)pc.dt;
@@ -43,28 +43,31 @@ __device__ KnotVal<R> knot_value(const PlanConst& pc, const Sky<R>& sky, double 
   return v;
 }
 
+// Cubic Hermite coefficients over an interval of H grid points; iH = 1/H
+// (H a power of two: exact).
 template <typename R>
-__device__ __forceinline__ void hermite(R f0, R d0, R f1, R d1, R H, R* c1, R* c2, R* c3) {
+__device__ __forceinline__ void hermite(R f0, R d0, R f1, R d1, R H, R iH, R* c1, R* c2, R* c3) {
   const R D = f1 - f0;
   *c1 = d0;
-  *c2 = (3 * D - (2 * d0 + d1) * H) / (H * H);
-  *c3 = (-2 * D + (d0 + d1) * H) / (H * H * H);
+  *c2 = (3 * D - (2 * d0 + d1) * H) * (iH * iH);
+  *c3 = (-2 * D + (d0 + d1) * H) * (iH * iH * iH);
 }
 
 __device__ __forceinline__ void write_record(KnotF* out, const KnotVal<double>& k0, const KnotVal<double>& k1, double H) {
   KnotF r;
+  const double iH = (double)1 / H;
   double c1, c2, c3;
   const double fl = floor(k0.U);
   r.I = (int32_t)fl;
   r.F = (float)(k0.U - fl);
-  hermite(k0.U, k0.dU, k1.U, k1.dU, H, &c1, &c2, &c3);
+  hermite(k0.U, k0.dU, k1.U, k1.dU, H, iH, &c1, &c2, &c3);
   r.u1 = (float)(c1 - 1.0); r.u2 = (float)c2; r.u3 = (float)c3;
   r.P = (float)(k0.P - floor(k0.P));
-  hermite(k0.P, k0.dP, k1.P, k1.dP, H, &c1, &c2, &c3);
+  hermite(k0.P, k0.dP, k1.P, k1.dP, H, iH, &c1, &c2, &c3);
   r.p1 = (float)c1; r.p2 = (float)c2; r.p3 = (float)c3;
-  hermite(k0.a, k0.da, k1.a, k1.da, H, &c1, &c2, &c3);
+  hermite(k0.a, k0.da, k1.a, k1.da, H, iH, &c1, &c2, &c3);
   r.a0 = (float)k0.a; r.a1 = (float)c1; r.a2 = (float)c2; r.a3 = (float)c3;
-  hermite(k0.b, k0.db, k1.b, k1.db, H, &c1, &c2, &c3);
+  hermite(k0.b, k0.db, k1.b, k1.db, H, iH, &c1, &c2, &c3);
   r.b0 = (float)k0.b; r.b1 = (float)c1; r.b2 = (float)c2; r.b3 = (float)c3;
   r.r0 = r.r1 = r.r2 = 0.f;
   *out = r;
@@ -73,18 +76,19 @@ __device__ __forceinline__ void write_record(KnotF* out, const KnotVal<double>& 
 // FP32 time map (precision study): the same record built from FP32 values.
 __device__ __forceinline__ void write_record(KnotF* out, const KnotVal<float>& k0, const KnotVal<float>& k1, float H) {
   KnotF r;
+  const float iH = (float)1 / H;
   float c1, c2, c3;
   const float fl = floorf(k0.U);
   r.I = (int32_t)fl;
   r.F = k0.U - fl;
-  hermite(k0.U, k0.dU, k1.U, k1.dU, H, &c1, &c2, &c3);
+  hermite(k0.U, k0.dU, k1.U, k1.dU, H, iH, &c1, &c2, &c3);
   r.u1 = c1 - 1.f; r.u2 = c2; r.u3 = c3;
   r.P = k0.P - floorf(k0.P);
-  hermite(k0.P, k0.dP, k1.P, k1.dP, H, &c1, &c2, &c3);
+  hermite(k0.P, k0.dP, k1.P, k1.dP, H, iH, &c1, &c2, &c3);
   r.p1 = c1; r.p2 = c2; r.p3 = c3;
-  hermite(k0.a, k0.da, k1.a, k1.da, H, &c1, &c2, &c3);
+  hermite(k0.a, k0.da, k1.a, k1.da, H, iH, &c1, &c2, &c3);
   r.a0 = k0.a; r.a1 = c1; r.a2 = c2; r.a3 = c3;
-  hermite(k0.b, k0.db, k1.b, k1.db, H, &c1, &c2, &c3);
+  hermite(k0.b, k0.db, k1.b, k1.db, H, iH, &c1, &c2, &c3);
   r.b0 = k0.b; r.b1 = c1; r.b2 = c2; r.b3 = c3;
   r.r0 = r.r1 = r.r2 = 0.f;
   *out = r;
@@ -92,16 +96,17 @@ __device__ __forceinline__ void write_record(KnotF* out, const KnotVal<float>& k
 
 __device__ __forceinline__ void write_record(KnotD* out, const KnotVal<double>& k0, const KnotVal<double>& k1, double H) {
   KnotD r;
+  const double iH = (double)1 / H;
   double c1, c2, c3;
   r.U = k0.U;
-  hermite(k0.U, k0.dU, k1.U, k1.dU, H, &c1, &c2, &c3);
+  hermite(k0.U, k0.dU, k1.U, k1.dU, H, iH, &c1, &c2, &c3);
   r.u1 = c1 - 1.0; r.u2 = c2; r.u3 = c3;
   r.P = k0.P - floor(k0.P);
-  hermite(k0.P, k0.dP, k1.P, k1.dP, H, &c1, &c2, &c3);
+  hermite(k0.P, k0.dP, k1.P, k1.dP, H, iH, &c1, &c2, &c3);
   r.p1 = c1; r.p2 = c2; r.p3 = c3;
-  hermite(k0.a, k0.da, k1.a, k1.da, H, &c1, &c2, &c3);
+  hermite(k0.a, k0.da, k1.a, k1.da, H, iH, &c1, &c2, &c3);
   r.a0 = k0.a; r.a1 = c1; r.a2 = c2; r.a3 = c3;
-  hermite(k0.b, k0.db, k1.b, k1.db, H, &c1, &c2, &c3);
+  hermite(k0.b, k0.db, k1.b, k1.db, H, iH, &c1, &c2, &c3);
   r.b0 = k0.b; r.b1 = c1; r.b2 = c2; r.b3 = c3;
   *out = r;
 }
