@@ -20,6 +20,12 @@ namespace fs {
 
 enum { SRC_LOAD = 0, SRC_NN = 1, SRC_SINC = 2 };
 
+// Bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a
+// multiple of 16): issued by one thread, completes in the background.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 template <typename R>
 struct ColsArgs {
   PlanConst pc;
@@ -384,6 +390,23 @@ __global__ void __launch_bounds__(NT, (blocks_for_smem(rows_smem<R, L2, RR>())))
     const int blk = w - tq * a.blocks_max;
     const int t = a.ti >= 0 ? a.ti : tq;
     const TmplMeta& m = a.c.meta[t];
+    {
+      // the next row block's two runs of the intermediate, into L2
+      const int wn = w + gridDim.x;
+      if (threadIdx.x == 0 && wn < total) {
+        const int tqn = wn / a.blocks_max;
+        const int tn = a.ti >= 0 ? a.ti : tqn;
+        const int blkn = wn - tqn * a.blocks_max;
+        const int ln = a.c.meta[tn].log2n;
+        if (blkn * RR < (1 << (ln - L2))) {
+          const cpx<R>* pz = reinterpret_cast<const cpx<R>*>(a.c.za) + (int64_t)tn * a.c.z_stride +
+                             (int64_t)blkn * ((1 << L2) * RR);
+          constexpr unsigned bytes = (unsigned)((1u << L2) * RR * sizeof(cpx<R>));
+          prefetch_l2(pz, bytes);
+          prefetch_l2(pz + ((int64_t)1 << ln), bytes);
+        }
+      }
+    }
     if (blk * RR >= (1 << (m.log2n - L2))) continue;
     const cpx<R>* za = reinterpret_cast<const cpx<R>*>(a.c.za) + (int64_t)t * a.c.z_stride;
     rows_tile<R, L2, RR, NT>(a, t, blk, buf, za);
