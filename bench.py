@@ -148,7 +148,7 @@ def fp32_peak_tflops(sm_mhz: float) -> float:
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def algorithmic_per_template(desc, fused=True):
+def algorithmic_per_template(desc, fused=True, l1=None):
     """(FLOPs, design bytes) of one template in each kernel.
 
     FLOPs, counted from the algorithm:
@@ -168,9 +168,8 @@ def algorithmic_per_template(desc, fused=True):
     The path's own algorithmic bytes are 8 N_d + 4 N (path_bytes)."""
     n = int(desc.n_fft)
     L = int(math.log2(n))
-    l1 = min(12, (L + 1) // 2)
-    if L - l1 > 12:
-        l1 = L - 12
+    if l1 is None:
+        l1 = max(6, min(12, L - 6))       # the library's default factorisation
     l2 = L - l1
     taps = desc.taps if desc.interp == 1 else 1
     nd = float(desc.n_data)
@@ -261,6 +260,8 @@ def main():
                     help="library execution mode")
     ap.add_argument("--chunk", type=int, default=0,
                     help="templates per internal launch (0: the library's default)")
+    ap.add_argument("--log2-n1", type=int, default=0,
+                    help="log2 of the first-pass FFT length (0: the library's default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -299,8 +300,8 @@ def main():
     plan = fs.Plan(desc, device=dev)
     mode = {"fused": fs.MODE_FUSED, "split": fs.MODE_SPLIT, "persistent": fs.MODE_PERSISTENT,
             "plain": fs.MODE_PLAIN}[args.mode]
-    if args.chunk or mode != fs.MODE_SPLIT:
-        plan.set_tuning(mode=mode, chunk=args.chunk)
+    if args.chunk or args.log2_n1 or mode != fs.MODE_SPLIT:
+        plan.set_tuning(mode=mode, chunk=args.chunk, log2_n1=args.log2_n1)
     stream = torch.cuda.Stream(device=dev)
     x = torch.from_numpy(x_np.astype(np.complex64)).to(dev)
     gaps = torch.from_numpy(gaps_np.reshape(-1).copy()).to(dev)
@@ -353,7 +354,8 @@ def main():
     peak_gbs, peak_kind = measured_peaks()
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     peak_tf = fp32_peak_tflops(sm_mhz)
-    per_tpl = algorithmic_per_template(desc, fused=mode in (fs.MODE_FUSED, fs.MODE_PERSISTENT))
+    per_tpl = algorithmic_per_template(desc, fused=mode in (fs.MODE_FUSED, fs.MODE_PERSISTENT),
+                                       l1=plan.tuning()["log2_n1"])
     kernels = {}
     for k in ("timemap", "resample", "fft_cols", "fft_rows", "persistent", "sums"):
         k_ms, k_n = prof[k]

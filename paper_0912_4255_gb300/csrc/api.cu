@@ -66,12 +66,7 @@ int ilog2(int64_t n) {
 int choose_shape(fstat_plan_s* p) {
   const int L = p->log2n;
   int l1 = p->tune.log2_n1;
-  if (l1 == 0) {
-    l1 = (L + 1) / 2;
-    if (l1 > 12) l1 = 12;
-    if (L - l1 > 12) l1 = L - 12;
-    if (l1 < 6) l1 = 6;
-  }
+  if (l1 == 0) l1 = default_log2_n1(L);
   const int l2 = L - l1;
   if (l1 < 6 || l1 > 12 || l2 < 6 || l2 > 12) return FSTAT_ENOTSUP;
   p->sh.log2n = L;

@@ -932,6 +932,16 @@ struct Shape {
   int log2n, l1, l2, cols, rows;
 };
 
+// Default factorisation N = N1 N2 of the four-step FFT: the longest first
+// pass (N1 <= 2^12, N2 >= 2^6), so that a second-pass block holds as many
+// rows as its shared memory allows and its 2F stores form longer runs.
+__host__ __device__ inline int default_log2_n1(int L) {
+  int l1 = L - 6;
+  if (l1 > 12) l1 = 12;
+  if (l1 < 6) l1 = 6;
+  return l1;
+}
+
 cudaError_t launch_timemap(const PlanConst& pc, const Chunk& c, int log2n_plan, int mode,
                            const int64_t* gaps, int64_t n_gaps_total, int* status,
                            int64_t tmpl_base, cudaStream_t s);

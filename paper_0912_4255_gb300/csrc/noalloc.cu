@@ -179,10 +179,7 @@ extern "C" int fstat_compute_noalloc(const fstat_plan_desc* d, const float* x_h,
   int L = 0;
   while (((int64_t)1 << L) < d->n_fft) ++L;
   Shape sh;
-  int l1 = (L + 1) / 2;
-  if (l1 > 12) l1 = 12;
-  if (L - l1 > 12) l1 = L - 12;
-  if (l1 < 6) l1 = 6;
+  const int l1 = default_log2_n1(L);
   sh.log2n = L; sh.l1 = l1; sh.l2 = L - l1;
   if (sh.l2 < 6 || sh.l2 > 12) return FSTAT_ENOTSUP;
   sh.cols = cols_per_block(pc.precision, sh.l1);

@@ -75,13 +75,7 @@ __device__ __forceinline__ void signal_done(int* ctr) {
   }
 }
 
-__device__ __forceinline__ int l1_of(int L) {
-  int l1 = (L + 1) / 2;
-  if (l1 > 12) l1 = 12;
-  if (L - l1 > 12) l1 = L - 12;
-  if (l1 < 6) l1 = 6;
-  return l1;
-}
+__device__ __forceinline__ int l1_of(int L) { return default_log2_n1(L); }
 
 // Each tile shape is its own (not inlined) function, so that its register
 // allocation does not have to cover the other shapes.

@@ -87,12 +87,19 @@ cudaError_t dispatch(const PlanConst& pc, const Chunk& c, int ti, int log2n, con
 template <typename R> constexpr int tile_log2() { return std::is_same<R, float>::value ? 11 : 10; }
 constexpr int kTilesPerBlock = 4;
 
-__host__ __device__ __forceinline__ int tile_log2_cols(int l2) { return l2 < 8 ? l2 : 8; }
+// log2 of the tile width TC: at most 256 and N2, and small enough that a
+// tile keeps TR >= 16 / C rows, so that its stores form runs of at least 16
+// values (TR * C) per column group.
+__host__ __device__ __forceinline__ int tile_log2_cols(int l2, int lc, int lp) {
+  int ltc = l2 < 8 ? l2 : 8;
+  if (ltc > lp - 4 + lc) ltc = lp - 4 + lc;
+  return ltc;
+}
 
 // number of tiles with a point below n_b
-__host__ __device__ __forceinline__ int live_tiles(int64_t n_b, int l2, int lp) {
+__host__ __device__ __forceinline__ int live_tiles(int64_t n_b, int l2, int lc, int lp) {
   if (n_b <= 0) return 0;
-  const int ltc = tile_log2_cols(l2);
+  const int ltc = tile_log2_cols(l2, lc, lp);
   const int64_t span = (int64_t)1 << (lp - ltc + l2);    // points of one row tile, TR N2
   const int ncol = 1 << (l2 - ltc);
   const int64_t rt = (n_b - 1) / span;
@@ -116,8 +123,8 @@ k_resample_t(PlanConst pc, Chunk c, int l2, int lc, const float2* __restrict__ x
   if (m.status != FSTAT_OK) return;
   const int L = m.log2n;
   const int n_b = (int)m.n_b;
-  const int nlive = live_tiles(m.n_b, l2, LP);
-  const int ltc = tile_log2_cols(l2);          // log2 TC
+  const int nlive = live_tiles(m.n_b, l2, lc, LP);
+  const int ltc = tile_log2_cols(l2, lc, LP);  // log2 TC
   const int TC = 1 << ltc;
   const int TR = P >> ltc;
   const Knot* kn = reinterpret_cast<const Knot*>(c.knots) + (int64_t)t * c.knot_stride;
@@ -170,11 +177,11 @@ k_resample_t(PlanConst pc, Chunk c, int l2, int lc, const float2* __restrict__ x
 // sized from a bound on n_b) is reported as FSTAT_ERANGE.
 constexpr int kSumThreads = 256;
 __global__ void __launch_bounds__(kSumThreads)
-k_sums_t(Chunk c, int l2, int lp, int covered, double sigma2, int* status) {
+k_sums_t(Chunk c, int l2, int lc, int lp, int covered, double sigma2, int* status) {
   __shared__ double sh[3][kSumThreads];
   TmplMeta* m = c.meta + blockIdx.x;
   if (m->status != FSTAT_OK) return;
-  const int nlive = live_tiles(m->n_b, l2, lp);
+  const int nlive = live_tiles(m->n_b, l2, lc, lp);
   if (nlive > covered) {
     if (threadIdx.x == 0) { m->status = FSTAT_ERANGE; set_status(status, FSTAT_ERANGE); }
     return;
@@ -207,9 +214,15 @@ int64_t nb_bound(const PlanConst& pc, int64_t n_fft) {
   return nb < n_fft ? nb : n_fft;
 }
 
+int log2_cols(const Shape& sh) {
+  int lc = 0;
+  while ((1 << lc) < sh.cols) ++lc;
+  return lc;
+}
+
 template <typename R>
 int resample_blocks(const PlanConst& pc, const Shape& sh) {
-  const int covered = live_tiles(nb_bound(pc, (int64_t)1 << sh.log2n), sh.l2, tile_log2<R>());
+  const int covered = live_tiles(nb_bound(pc, (int64_t)1 << sh.log2n), sh.l2, log2_cols(sh), tile_log2<R>());
   return (covered + kTilesPerBlock - 1) / kTilesPerBlock;
 }
 
@@ -217,8 +230,7 @@ int resample_blocks(const PlanConst& pc, const Shape& sh) {
 
 cudaError_t launch_resample_t(const PlanConst& pc, const Chunk& c, const Shape& sh, const float2* x,
                               const int64_t* gaps, const double* wcs, cudaStream_t s) {
-  int lc = 0;
-  while ((1 << lc) < sh.cols) ++lc;
+  const int lc = log2_cols(sh);
   if (pc.precision == FSTAT_PREC_FP64) {
     dim3 grid((unsigned)resample_blocks<double>(pc, sh), (unsigned)c.nt);
     if (grid.x == 0) return cudaSuccess;
@@ -245,7 +257,7 @@ cudaError_t launch_sums_t(const PlanConst& pc, const Chunk& c, const Shape& sh, 
   const bool d = pc.precision == FSTAT_PREC_FP64;
   const int lp = d ? tile_log2<double>() : tile_log2<float>();
   const int covered = (d ? resample_blocks<double>(pc, sh) : resample_blocks<float>(pc, sh)) * kTilesPerBlock;
-  k_sums_t<<<c.nt, kSumThreads, 0, s>>>(c, sh.l2, lp, covered, pc.sigma2, status);
+  k_sums_t<<<c.nt, kSumThreads, 0, s>>>(c, sh.l2, log2_cols(sh), lp, covered, pc.sigma2, status);
   return cudaGetLastError();
 }
 
