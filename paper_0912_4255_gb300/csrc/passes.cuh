@@ -239,13 +239,15 @@ __device__ __forceinline__ void cols_tile(const ColsArgs<R>& a, int t, int tile,
     for (int q = 1; q < RADL; ++q) x[q] = cmul(x[q], tlast[(q - 1) * NS + j]);
     Dft<Cx, RADL>::run(x);
     const int k2 = c0 + c;
-    Cx* zs = sr ? zb : za;
+    // p1 = j + q NS lands at Z[p1 / R][k2][p1 % R]; NS is a multiple of R, so
+    // consecutive q are N / RADL elements apart
+    Cx* zq = (sr ? zb : za) + ((((int64_t)(j >> lr) * N2 + k2) << lr) + (j & (RRr - 1)));
+    const int64_t zstep = ((int64_t)1 << L) / RADL;
     const Cx wj = ta[c * NS + j];
 #pragma unroll
     for (int q = 0; q < RADL; ++q) {
-      const int p1 = j + q * NS;
       const Cx w = q == 0 ? wj : cmul(wj, tb[c * RADL + q]);
-      zs[((int64_t)(p1 >> lr) * N2 + k2) * RRr + (p1 & (RRr - 1))] = cmul(x[q], w);
+      zq[q * zstep] = cmul(x[q], w);
     }
   }
 }
@@ -365,12 +367,15 @@ __device__ __forceinline__ void rows_tile(const RowsArgs<R>& a, int t, int blk, 
     }
     Dft<Cx, RADL>::run(fa);
     Dft<Cx, RADL>::run(fb);
+    // p2 = j + q NS goes to row (p2 + N2/2) mod N2: + N2/2 for the first half
+    // of q (p2 < N2/2), - N2/2 for the second
+    float* oq = out + (int64_t)(r0 + r) + (int64_t)N1 * j;
+    const int64_t s1 = (int64_t)N1 * NS, hh = (int64_t)N1 * (N2 / 2);
 #pragma unroll
     for (int q = 0; q < RADL; ++q) {
-      const int p2 = j + q * NS;
       const R v = ca * (fa[q].x * fa[q].x + fa[q].y * fa[q].y) + cb * (fb[q].x * fb[q].x + fb[q].y * fb[q].y)
                 + cc * (fa[q].x * fb[q].x + fa[q].y * fb[q].y);
-      __stcs(out + (int64_t)(r0 + r) + (int64_t)N1 * ((p2 + N2 / 2) & (N2 - 1)), (float)v);
+      __stcs(oq + q * s1 + (q < RADL / 2 ? hh : -hh), (float)v);
     }
   }
 }
