@@ -54,17 +54,18 @@ struct RowsArgs {
 
 // --------------------------------------------------------------- shapes
 
-// Points per block: 8k complex values in FP32 (64 KB of shared memory with
-// both series), 4k in FP64, so that two blocks share an SM; at most 16
-// columns (rows) per block.
-template <typename R> constexpr int points_per_block() { return std::is_same<R, float>::value ? 8192 : 4096; }
-template <typename R> constexpr int cols_for(int L1) {
-  const int c = (points_per_block<R>() / 2) >> L1;
+// Points per block (both series): 16k complex values in FP32 (128 KB of
+// shared memory, one block of 1024 threads per SM: the columns of a block
+// give Z runs of 64 B and 2F runs of 32 B), 4k in FP64 (two blocks per SM);
+// at most 16 columns (rows) per block.  P: the points of a block.
+template <typename R> constexpr int points_per_block() { return std::is_same<R, float>::value ? 16384 : 4096; }
+template <typename R, int P = points_per_block<R>()> constexpr int cols_for(int L1) {
+  const int c = (P / 2) >> L1;
   return c > 16 ? 16 : (c < 1 ? 1 : c);
 }
 template <typename R> constexpr int threads_for(int logn, int count) {
   const int units = (count << logn) / 16;
-  return units >= 512 ? 512 : (units < 32 ? 32 : units);
+  return units >= 1024 ? 1024 : (units < 32 ? 32 : units);
 }
 // Stage plan of pass A: shared-memory stages up to sub-transforms of 2^NSL_LAST,
 // then a last stage of radix 2^RBL in registers.  Its shared memory: both

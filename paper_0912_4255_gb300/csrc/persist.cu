@@ -19,6 +19,7 @@ namespace fs {
 namespace {
 
 constexpr int kPT = 512;          // threads per block
+constexpr int kPP = 8192;         // points per work item (both series)
 constexpr int kSlots = 3;         // intermediate slots in flight
 
 struct PersistArgs {
@@ -82,21 +83,21 @@ __device__ __forceinline__ int l1_of(int L) { return default_log2_n1(L); }
 template <int L1, int SRC, int TAPS>
 __device__ __noinline__ void cols_call(const ColsArgs<float>& a, int t, int tile, float2* buf, double* red,
                                        float2* za, int rr, int lr) {
-  cols_tables<float, L1, cols_for<float>(L1), kPT>(a.tw, buf);
-  cols_tile<float, L1, cols_for<float>(L1), kPT, SRC, TAPS>(a, t, tile, buf, red, za, rr, lr);
+  cols_tables<float, L1, cols_for<float, kPP>(L1), kPT>(a.tw, buf);
+  cols_tile<float, L1, cols_for<float, kPP>(L1), kPT, SRC, TAPS>(a, t, tile, buf, red, za, rr, lr);
 }
 template <int L2>
 __device__ __noinline__ void rows_call(const RowsArgs<float>& a, int t, int blk, float2* buf, const float2* za) {
-  rows_tables<float, L2, cols_for<float>(L2), kPT>(a.tw, buf);
+  rows_tables<float, L2, cols_for<float, kPP>(L2), kPT>(a.tw, buf);
   __syncthreads();
-  rows_tile<float, L2, cols_for<float>(L2), kPT>(a, t, blk, buf, za);
+  rows_tile<float, L2, cols_for<float, kPP>(L2), kPT>(a, t, blk, buf, za);
 }
 
 template <int SRC, int TAPS>
 __device__ __forceinline__ void run_cols(const PersistArgs& p, int t, int tile, float2* buf, double* red) {
   const int L = p.ca.c.meta[t].log2n;
   const int l1 = l1_of(L), l2 = L - l1;
-  const int rr = cols_for<float>(l2);
+  const int rr = cols_for<float, kPP>(l2);
   const int lr = 31 - __clz(rr);
   float2* za = p.zslots + (int64_t)(t % kSlots) * p.z_stride;
   switch (l1) {
@@ -168,7 +169,7 @@ __global__ void k_schedule(const TmplMeta* __restrict__ meta, int n_t, int* cnt,
     const TmplMeta& m = meta[t];
     const int L = m.log2n;
     const int l1 = l1_of(L), l2 = L - l1;
-    const int C = cols_for<float>(l1), RR = cols_for<float>(l2);
+    const int C = cols_for<float, kPP>(l1), RR = cols_for<float, kPP>(l2);
     cnt[t] = m.status == FSTAT_OK ? (1 << l2) / C : 0;
     cnt[n_t + t] = (1 << l1) / RR;
   }
@@ -218,7 +219,7 @@ int persist_slots() { return kSlots; }
 // Largest dynamic shared memory of any tile shape of either pass (FP32).
 size_t persist_smem() {
   size_t m = 0;
-#define FS_P_SM(V) { const size_t a = cols_smem<float, V, cols_for<float>(V)>(), b = rows_smem<float, V, cols_for<float>(V)>(); \
+#define FS_P_SM(V) { const size_t a = cols_smem<float, V, cols_for<float, kPP>(V)>(), b = rows_smem<float, V, cols_for<float, kPP>(V)>(); \
                        if (a > m) m = a; if (b > m) m = b; }
   FS_P_SM(6) FS_P_SM(7) FS_P_SM(8) FS_P_SM(9) FS_P_SM(10) FS_P_SM(11) FS_P_SM(12)
 #undef FS_P_SM
