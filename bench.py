@@ -262,6 +262,8 @@ def main():
                     help="templates per internal launch (0: the library's default)")
     ap.add_argument("--log2-n1", type=int, default=0,
                     help="log2 of the first-pass FFT length (0: the library's default)")
+    ap.add_argument("--copy-streams", type=int, default=4,
+                    help="streams the end-to-end leg splits each batch's device-to-host copy over")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -380,7 +382,8 @@ def main():
     # ---- end to end through the public API: pinned host in, pinned host out
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(fs, plan, desc, x_np, tm, gaps_np, dev, args, world, batch)
+        e2e = run_e2e(fs, plan, desc, x_np, tm, gaps_np, dev, args, world, batch,
+                      copy_streams=max(1, args.copy_streams))
 
     line = {
         "metric": "2F values/sec (templates x freq bins) at rel err <= 1e-4",
@@ -419,10 +422,12 @@ def main():
         dist.destroy_process_group()
 
 
-def run_e2e(fs, plan, desc, x_np, tm, gaps_np, dev, args, world, batch):
+def run_e2e(fs, plan, desc, x_np, tm, gaps_np, dev, args, world, batch, copy_streams=4):
     """Same metric with host buffers: per step the input series, templates and
     gap list go host->device and every 2F value comes back device->host into
-    pinned memory (double-buffered, copies overlapped with compute)."""
+    pinned memory (double-buffered, copies overlapped with compute; each
+    batch's copy is split over copy_streams streams so that several copy
+    engines move it)."""
     import torch
     n_t = len(tm)
     n_fft = int(desc.n_fft)
@@ -435,11 +440,13 @@ def run_e2e(fs, plan, desc, x_np, tm, gaps_np, dev, args, world, batch):
     t_d = torch.empty_like(t_h, device=dev)
     outs = [torch.empty(batch * n_fft, dtype=torch.float32, device=dev) for _ in range(2)]
     host = [torch.empty(batch * n_fft, dtype=torch.float32).pin_memory() for _ in range(2)]
-    cs, xs = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    cs = torch.cuda.Stream(device=dev)
+    xss = [torch.cuda.Stream(device=dev) for _ in range(copy_streams)]
     done = [torch.cuda.Event() for _ in range(2)]
-    copied = [torch.cuda.Event() for _ in range(2)]
-    for e in copied:
-        e.record(xs)
+    copied = [[torch.cuda.Event() for _ in xss] for _ in range(2)]
+    for ev in copied:
+        for e, xs in zip(ev, xss):
+            e.record(xs)
 
     def step():
         with torch.cuda.stream(cs):
@@ -449,13 +456,19 @@ def run_e2e(fs, plan, desc, x_np, tm, gaps_np, dev, args, world, batch):
             for i, b0 in enumerate(range(0, n_t, batch)):
                 nb = min(batch, n_t - b0)
                 j = i & 1
-                cs.wait_event(copied[j])
+                for e in copied[j]:
+                    cs.wait_event(e)
                 fs.fstat_compute(plan, x_d, t_d[b0 * tsize:(b0 + nb) * tsize], g_d, outs[j], stream=cs)
                 done[j].record(cs)
-                xs.wait_event(done[j])
-                with torch.cuda.stream(xs):
-                    host[j][:nb * n_fft].copy_(outs[j][:nb * n_fft], non_blocking=True)
-                copied[j].record(xs)
+                total = nb * n_fft
+                part = (total + len(xss) - 1) // len(xss)
+                for k, xs in enumerate(xss):
+                    a0, a1 = k * part, min(total, (k + 1) * part)
+                    xs.wait_event(done[j])
+                    if a1 > a0:
+                        with torch.cuda.stream(xs):
+                            host[j][a0:a1].copy_(outs[j][a0:a1], non_blocking=True)
+                    copied[j][k].record(xs)
 
     for _ in range(min(args.warmup, 1)):
         step()

@@ -100,6 +100,29 @@ def test_unfused_and_fused_agree(mode, interp):
         assert r15(b[i], oracle_two_f(d, x, tm[i])) <= TOL
 
 
+def test_split_mode_every_factorisation():
+    """The tiled resampler and both passes at every first-pass length of a
+    2^18 FFT (N1 = 2^6 .. 2^12: columns per block from 16 down to 2, rows
+    per second-pass block from 1 up to 16, tile widths from 128 to 256):
+    every shape against the oracle, and the shapes against each other."""
+    d = synth.PlanDesc(dt=0.5, n_data=120_001, n_fft=1 << 18, interp=R.SINC, f_het=120.0,
+                       max_templates=2)
+    gaps = synth.gap_intervals(d.n_data, 0.1, 3600, 9000, seed=17)
+    x, _ = injected_series(d, 18, [synth.random_injection(19, df=-0.3)], gaps)
+    tm = synth.make_templates([0.7, 3.9], [-0.4, 0.9], [-1e-9, 0.0], [0, 1001], [d.n_data, 100_000],
+                              0, len(gaps))
+    refs = [oracle_two_f(d, x, tm[i], gaps) for i in range(2)]
+    outs = []
+    for l1 in (6, 8, 10, 12):
+        got, rc = run_compute(d, x, tm, gaps, mode=MODES["split"], tuning={"log2_n1": l1})
+        assert rc == 0, l1
+        for i in range(2):
+            assert r15(got[i], refs[i]) <= TOL, (l1, i)
+        outs.append(got)
+    for got in outs[1:]:
+        assert r15(got, outs[0]) < 1e-5
+
+
 @pytest.mark.parametrize("mode", ["fused", "split"])
 def test_fp64_mode_tight(mode):
     """All-FP64 path: agreement with the FP64 oracle to 1e-6 (the floor is the
