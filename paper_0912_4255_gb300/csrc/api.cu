@@ -81,9 +81,11 @@ int choose_shape(fstat_plan_s* p) {
   if (p->pc.log2h < 4 || p->pc.log2h > 14) return FSTAT_ERANGE;
   const int64_t n = (int64_t)1 << L;
   const int64_t zbytes = 2 * n * p->cplx_bytes;
+  // templates per internal batch: by default 4 GiB of FFT intermediate (64
+  // templates at 2^22; the split mode adds as much for the resampled series)
   int ch = p->tune.chunk;
   if (ch <= 0) {
-    ch = (int)((int64_t)(1ll << 30) / zbytes);
+    ch = (int)((int64_t)(4ll << 30) / zbytes);
     if (ch < 1) ch = 1;
   }
   if (p->tune.mode == FSTAT_MODE_PLAIN) ch = 1;
