@@ -269,6 +269,29 @@ __global__ void __launch_bounds__(NT, (blocks_for_smem(cols_smem<R, L1, C>()))) 
     const int tile = w - tq * a.tiles_max;
     const int t = a.ti >= 0 ? a.ti : tq;
     const TmplMeta& m = a.c.meta[t];
+    if constexpr (SRC == SRC_LOAD) {
+      // the rows below n_b of the next tile's resampled block, into L2 (one
+      // block per SM: nothing else hides the latency of the first stage)
+      const int wn = w + gridDim.x;
+      if (threadIdx.x == 0 && wn < total) {
+        const int tqn = wn / a.tiles_max;
+        const int tn = a.ti >= 0 ? a.ti : tqn;
+        const int tilen = wn - tqn * a.tiles_max;
+        const TmplMeta& mn = a.c.meta[tn];
+        const int ln = mn.log2n;
+        if (mn.status == FSTAT_OK && tilen < (1 << (ln - L1)) / C) {
+          const int64_t first = (int64_t)tilen * C;                        // c0 of that tile
+          const int64_t rows = mn.n_b > first ? (mn.n_b - first + (1 << (ln - L1)) - 1) >> (ln - L1) : 0;
+          const unsigned bytes = (unsigned)((rows < (1 << L1) ? rows : (1 << L1)) * C * sizeof(cpx<R>));
+          if (bytes >= 16) {
+            const cpx<R>* pa = reinterpret_cast<const cpx<R>*>(a.c.wa) + (int64_t)tn * a.c.z_stride +
+                               first * (1 << L1);
+            prefetch_l2(pa, bytes & ~15u);
+            prefetch_l2(pa + ((int64_t)1 << ln), bytes & ~15u);
+          }
+        }
+      }
+    }
     if (tile >= (1 << (m.log2n - L1)) / C || m.status != FSTAT_OK) continue;
     cpx<R>* za = reinterpret_cast<cpx<R>*>(a.c.za) + (int64_t)t * a.c.z_stride;
     cols_tile<R, L1, C, NT, SRC, TAPS>(a, t, tile, buf, red, za, a.rr, a.log2rr);
