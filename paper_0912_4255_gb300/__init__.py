@@ -258,7 +258,11 @@ class GraphRunner:
             fstat_compute(plan, x_h, templates, gaps, self.twoF, stream=self.stream)
 
     def replay(self):
-        self.graph.replay()
+        """Replay on the runner's stream (synchronise it, or the device,
+        before reading twoF)."""
+        import torch
+        with torch.cuda.stream(self.stream):
+            self.graph.replay()
         return self.twoF
 
 

@@ -57,6 +57,41 @@ def test_persistent_ragged_batch_matches_oracle():
         assert r15(got[o:o + n], ref) <= TOL, i
 
 
+def test_ragged_batch_in_split_groups():
+    """The same kind of ragged batch through RaggedBatch (one split-mode plan
+    per FFT length, every 2F at its template's out_off, replayed from a CUDA
+    graph) against the oracle, and against the persistent launch."""
+    import torch
+    import paper_0912_4255_gb300 as fs
+    from paper_0912_4255_gb300.batch import RaggedBatch
+    desc = synth.PlanDesc(dt=0.5, n_data=86400, n_fft=1 << 17, interp=R.SINC, f_het=100.0,
+                          max_templates=12)
+    tm, gaps, nf = _ragged_batch(12, 63, desc)
+    assert len(set(nf.tolist())) >= 2
+    x = _data(desc, 64, gaps)
+    dev = torch.device("cuda:0")
+    xd = torch.from_numpy(x).to(dev)
+    gd = torch.from_numpy(gaps.reshape(-1).copy()).to(dev)
+    rb = RaggedBatch(desc, xd, tm, gd, device=dev, slice_templates=4, graph=True)
+    rb.twoF.fill_(float("nan"))
+    torch.cuda.synchronize()
+    rb.run()
+    assert rb.status() == 0                   # synchronises the batch's stream
+    got = rb.twoF.cpu().numpy()
+    for i in range(len(tm)):
+        o, n = int(tm["out_off"][i]), int(nf[i])
+        g = gaps[int(tm["gap_off"][i]):int(tm["gap_off"][i]) + int(tm["n_gaps"][i])]
+        ref = F.resample_two_f(x.astype(np.complex128), tm[i], g, desc, n_fft=n)
+        assert r15(got[o:o + n], ref) <= TOL, i
+    plan = fs.Plan(desc)
+    plan.set_tuning(mode=fs.MODE_PERSISTENT)
+    per = torch.empty_like(rb.twoF)
+    fs.fstat_compute(plan, xd, fs.pack_templates(tm, device=dev), gd, per)
+    assert fs.fstat_status(plan, raise_error=False) == 0
+    assert r15(got, per.cpu().numpy()) < 1e-5
+    rb.close()
+
+
 def test_persistent_equals_fused_and_graph_replay():
     import torch
     import paper_0912_4255_gb300 as fs
