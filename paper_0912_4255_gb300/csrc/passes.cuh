@@ -1,6 +1,7 @@
 // The two passes of the four-step FFT that evaluates Eqs. 19-20 for every
-// bin, with steps 2-5 of Sec. III.A.2 fused into the first pass and Eq. 6
-// fused into the second.
+// bin.  Steps 2-5 of Sec. III.A.2 are either fused into the first pass (fused
+// and persistent modes) or done by the tiled resampler, whose output the
+// first pass loads (split mode); Eq. 6 is fused into the second pass.
 //
 // N = N1 N2, k = k2 + N2 k1, p = p1 + N1 p2:
 //   X[p1 + N1 p2] = sum_k2 W_N2^{p2 k2} W_N^{p1 k2} sum_k1 x[k2 + N2 k1] W_N1^{p1 k1}.
@@ -55,9 +56,10 @@ struct RowsArgs {
 // --------------------------------------------------------------- shapes
 
 // Points per block (both series): 16k complex values in FP32 (128 KB of
-// shared memory, one block of 1024 threads per SM: the columns of a block
-// give Z runs of 64 B and 2F runs of 32 B), 4k in FP64 (two blocks per SM);
-// at most 16 columns (rows) per block.  P: the points of a block.
+// shared memory, one block of 1024 threads per SM; at N = 2^22 a first-pass
+// block's C = 2 columns and a second-pass block's R = 8 rows give Z runs of
+// R C values = 128 B and 2F runs of R values = 32 B), 4k in FP64 (two blocks
+// per SM); at most 16 columns (rows) per block.  P: the points of a block.
 template <typename R> constexpr int points_per_block() { return std::is_same<R, float>::value ? 16384 : 4096; }
 template <typename R, int P = points_per_block<R>()> constexpr int cols_for(int L1) {
   const int c = (P / 2) >> L1;
