@@ -267,6 +267,9 @@ def main():
     ap.add_argument("--workload", default="search", choices=["search", "batch"],
                     help="search: the 8192-template grid (the metric's workload); batch: 4096 "
                          "templates with uneven spans, own gap lists and FFT lengths")
+    ap.add_argument("--topk", type=int, default=16,
+                    help="candidates per band for the e2e_candidates leg (0: skip it)")
+    ap.add_argument("--topk-band", type=int, default=65536, help="bins per candidate band")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -418,6 +421,9 @@ def main():
     }
     if e2e is not None:
         line["e2e"] = e2e
+    if not args.no_e2e and args.topk > 0:
+        line["e2e_candidates"] = run_e2e_candidates(fs, plan, desc, x_np, tm, gaps_np, dev, args, world,
+                                                    batch, args.topk_band, args.topk)
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
@@ -489,6 +495,51 @@ def run_e2e(fs, plan, desc, x_np, tm, gaps_np, dev, args, world, batch, copy_str
     return {"value": n_t * n_fft * world / wall, "unit": "2F values/s",
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "ms_per_step": wall * 1e3, "steps": steps}
+
+
+def run_e2e_candidates(fs, plan, desc, x_np, tm, gaps_np, dev, args, world, batch, band_len, k):
+    """End to end through the public API for a search that keeps candidates:
+    per step the inputs go host->device, every 2F value is computed in device
+    memory, fstat_topk keeps the k loudest bins of every band, and only those
+    (values and bins) come back to pinned host memory."""
+    import torch
+    n_t = len(tm)
+    n_fft = int(desc.n_fft)
+    tsize = fs.TEMPLATE_DTYPE.itemsize
+    x_h = torch.from_numpy(x_np.astype(np.complex64)).pin_memory()
+    g_h = torch.from_numpy(gaps_np.reshape(-1).copy()).pin_memory()
+    t_h = fs.pack_templates(tm, device=None).pin_memory()
+    x_d, g_d, t_d = (torch.empty_like(h, device=dev) for h in (x_h, g_h, t_h))
+    out = torch.empty(batch * n_fft, dtype=torch.float32, device=dev)
+    n_bands = n_fft // band_len
+    hv = torch.empty((n_t, n_bands, k), dtype=torch.float32).pin_memory()
+    hb = torch.empty((n_t, n_bands, k), dtype=torch.int32).pin_memory()
+    cs = torch.cuda.Stream(device=dev)
+
+    def step():
+        with torch.cuda.stream(cs):
+            x_d.copy_(x_h, non_blocking=True)
+            g_d.copy_(g_h, non_blocking=True)
+            t_d.copy_(t_h, non_blocking=True)
+            for b0 in range(0, n_t, batch):
+                nb = min(batch, n_t - b0)
+                fs.fstat_compute(plan, x_d, t_d[b0 * tsize:(b0 + nb) * tsize], g_d, out, stream=cs)
+                v, b = fs.fstat_topk(out[:nb * n_fft], band_len, k, n_rows=nb, stream=cs)
+                hv[b0:b0 + nb].copy_(v, non_blocking=True)
+                hb[b0:b0 + nb].copy_(b, non_blocking=True)
+
+    step()
+    torch.cuda.synchronize(dev)
+    steps = max(1, min(args.steps, 2))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize(dev)
+    wall = (time.perf_counter() - t0) / steps
+    return {"value": n_t * n_fft * world / wall, "unit": "2F values/s",
+            "h2d_bytes_per_step": int(x_h.numel() * 8 + g_h.numel() * 8 + t_h.numel()),
+            "d2h_bytes_per_step": int(hv.numel() * 4 + hb.numel() * 4),
+            "ms_per_step": wall * 1e3, "steps": steps, "band_len": band_len, "k": k}
 
 
 def run_batch(args):

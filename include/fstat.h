@@ -236,6 +236,22 @@ int fstat_compute_noalloc(const fstat_plan_desc *d, const float *x_h, const fsta
                           int64_t n_t, const int64_t *gaps, int64_t n_gaps_total, float *twoF,
                           void *stream);
 
+/* Per-band top-k candidates of 2F spectra.  The paper computes 2F in every
+ * frequency bin (Eq. 6, step 7 of Sec. III.A.2) for searches over many
+ * frequencies and defines no candidate stage; this is the step after it that
+ * a search applies: for each of n_rows rows of row_len values in twoF (e.g.
+ * fstat_compute's output, row_len = n_fft) and each band of band_len
+ * consecutive bins, the k largest values in descending order (ties: the
+ * lower bin first) and their bin indices within the row.  NaN bins are
+ * skipped; a band with fewer than k finite values is padded with (-inf, -1).
+ * twoF: device, 16-byte aligned; val float32 and bin int32, device, laid out
+ * [n_rows][row_len / band_len][k].  band_len a multiple of 2048 that divides
+ * row_len, 1 <= k <= 64.  Errors: EINVAL (null or misaligned pointers, bad
+ * sizes), ERANGE (more than 65535 rows or bands), ECUDA.  Asynchronous on
+ * stream; needs no plan. */
+int fstat_topk(const float *twoF, int64_t n_rows, int64_t row_len, int64_t band_len, int k,
+               float *val, int32_t *bin, void *stream);
+
 /* Synchronise the stream, return and clear the first device-side error
  * recorded since the last call (FSTAT_OK if none). */
 int fstat_status(fstat_plan_t p, void *stream);

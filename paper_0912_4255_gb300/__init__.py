@@ -24,7 +24,7 @@ __all__ = [
     "FstatError", "Plan", "fstat_plan", "fstat_compute", "fstat_compute_noalloc", "fstat_resample",
     "fstat_grad",
     "fstat_status", "fstat_destroy", "fstat_strerror", "fstat_template_nb", "pack_templates",
-    "fstat_profile", "fstat_profile_read", "KERNEL_KINDS", "GraphRunner", "fstat_debug_stall",
+    "fstat_profile", "fstat_profile_read", "KERNEL_KINDS", "GraphRunner", "fstat_debug_stall", "fstat_topk",
     "NEAREST", "SINC", "WIN_RECT", "WIN_LANCZOS", "PREC_MIXED", "PREC_FP64", "PREC_FP32",
     "MODE_FUSED", "MODE_PLAIN", "MODE_PERSISTENT", "MODE_SPLIT", "TEMPLATE_DTYPE",
 ]
@@ -214,6 +214,22 @@ def fstat_grad(plan: Plan, x_h, templates, df, gaps=None, stream=None):
 
 
 KERNEL_KINDS = ("timemap", "resample", "fft_cols", "fft_rows", "grad_fwd", "grad_adj", "persistent", "sums")
+
+
+def fstat_topk(two_f, band_len: int, k: int, n_rows: int | None = None, stream=None):
+    """Per-band top-k candidates of 2F rows (``two_f`` device float32 of
+    n_rows x row_len, row_len = numel / n_rows): returns (values float32,
+    bins int32), each [n_rows, row_len // band_len, k], descending."""
+    import torch
+    lib = _lib.load()
+    n_rows = 1 if n_rows is None else int(n_rows)
+    row_len = two_f.numel() // n_rows
+    n_bands = row_len // band_len if band_len else 0
+    val = torch.empty((n_rows, n_bands, k), dtype=torch.float32, device=two_f.device)
+    bins = torch.empty((n_rows, n_bands, k), dtype=torch.int32, device=two_f.device)
+    _check(lib.fstat_topk(_ptr(two_f), n_rows, row_len, int(band_len), int(k), _ptr(val), _ptr(bins),
+                          _stream(stream)), "fstat_topk")
+    return val, bins
 
 
 def fstat_profile(plan: Plan, enable: bool = True):

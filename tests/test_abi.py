@@ -105,3 +105,16 @@ def test_null_arguments(lib):
     assert lib.fstat_status(None, None) == -1
     assert lib.fstat_compute(None, None, None, 0, None, 0, None, None) == -1
     lib.fstat_destroy(None)
+
+
+def test_topk_rejects_bad_arguments_on_the_host(lib):
+    """fstat_topk checks its sizes and pointers before any launch."""
+    p = 4096          # a 16-byte aligned stand-in pointer (never dereferenced)
+    assert lib.fstat_topk(None, 1, 4096, 2048, 4, p, p, None) == -1          # null input
+    assert lib.fstat_topk(p + 4, 1, 4096, 2048, 4, p, p, None) == -1         # not 16-byte aligned
+    assert lib.fstat_topk(p, 1, 4096, 2048, 0, p, p, None) == -1             # k < 1
+    assert lib.fstat_topk(p, 1, 4096, 2048, 65, p, p, None) == -1            # k > 64
+    assert lib.fstat_topk(p, 1, 4096, 1024, 4, p, p, None) == -1             # band below 2048
+    assert lib.fstat_topk(p, 1, 6144, 4096, 4, p, p, None) == -1             # band does not divide
+    assert lib.fstat_topk(p, 70000, 4096, 2048, 4, p, p, None) == -2         # too many rows
+    assert lib.fstat_topk(p, 0, 4096, 2048, 4, p, p, None) == 0              # nothing to do

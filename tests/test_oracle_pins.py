@@ -413,3 +413,40 @@ def test_fibonacci_sky_uniform():
     a, d = synth.fibonacci_sky(4096)
     assert abs(np.mean(np.sin(d))) < 1e-3
     assert np.all((a >= 0) & (a < 2 * math.pi))
+
+
+# --------------------------------------------------------------- candidates
+
+def test_band_top_k_against_brute_force():
+    """Per-band top-k (the step after Eq. 6 that a search applies): brute
+    force on small rows with ties and NaN bins."""
+    from oracle import candidates as CA
+    g = np.random.default_rng(11)
+    a = g.integers(0, 6, size=(3, 48)).astype(np.float64)     # many ties
+    a[1, 5] = np.nan
+    a[2, 16:32] = np.nan                                        # a band with no finite value
+    vals, bins = CA.band_top_k(a, 16, 5)
+    for r in range(3):
+        for b in range(3):
+            cand = [(a[r, j], j) for j in range(b * 16, (b + 1) * 16) if not np.isnan(a[r, j])]
+            cand.sort(key=lambda t: (-t[0], t[1]))               # largest first, then lower bin
+            want = cand[:5] + [(-np.inf, -1)] * (5 - len(cand[:5]))
+            assert [tuple(x) for x in zip(vals[r, b], bins[r, b])] == want
+
+
+def test_band_top_k_is_a_selection():
+    """Invariants: descending values, bins inside their band, the values are
+    the spectrum's at those bins, and nothing outside exceeds the k-th."""
+    from oracle import candidates as CA
+    g = np.random.default_rng(12)
+    a = g.chisquare(4, size=(2, 4096))
+    a[0, 1234] = 90.0
+    vals, bins = CA.band_top_k(a, 1024, 8)
+    assert np.all(np.diff(vals, axis=2) <= 0)
+    for r in range(2):
+        for b in range(4):
+            assert np.all((bins[r, b] >= b * 1024) & (bins[r, b] < (b + 1) * 1024))
+            assert np.array_equal(a[r, bins[r, b]], vals[r, b])
+            rest = np.delete(a[r, b * 1024:(b + 1) * 1024], bins[r, b] - b * 1024)
+            assert rest.max() <= vals[r, b, -1]
+    assert bins[0, 1, 0] == 1234 and vals[0, 1, 0] == 90.0
