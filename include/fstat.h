@@ -21,7 +21,8 @@
  *  - x_h = x exp(-2 pi i f_h (t - t_start)); the output bin q of a template
  *    holds the frequency offset df = (q - n_fft/2)/(n_fft dt) from f_het, in
  *    ascending order;
- *  - Phi_s(tau) = 2 pi fdot tau^2 / 2 with tau = t_b - t_start, removed by
+ *  - Phi_s(tau) = 2 pi (fdot tau^2 / 2 + fddot tau^3 / 6) with tau = t_b - t_start
+ *    (Eq. 4 to s = 2 in barycentric time), removed by
  *    multiplying with exp(-i Phi_s);
  *  - 2F = 2 (B|F_a|^2 + A|F_b|^2 - 2 C Re(F_a F_b*)) / (sigma2 D) with the
  *    masked sums A = sum m a^2, B = sum m b^2, C = sum m a b, D = A B - C^2
@@ -121,12 +122,14 @@ typedef struct fstat_plan_desc {
  * gaps[2*gap_off .. 2*(gap_off+n_gaps)) as sorted, disjoint [start, end)
  * sample pairs inside the span; n_fft: 0 for the plan's n_fft, else a power
  * of two <= the plan's (persistent mode only); out_off: offset of its 2F
- * values in the output array in floats, -1 for index * plan n_fft. */
+ * values in the output array in floats, -1 for index * plan n_fft; fddot:
+ * the second spindown (Hz/s^2, the s = 2 term of Eq. 4). */
 typedef struct fstat_template {
   double alpha, delta, fdot;
   int64_t span_start, span_len;
   int64_t gap_off, n_gaps;
   int64_t n_fft, out_off;
+  double fddot;
 } fstat_template;
 
 /* Kernel shape choices (set by the autotuner; zeros mean automatic).
@@ -168,7 +171,7 @@ int fstat_template_nb(fstat_plan_t p, const fstat_template *host_t, int64_t n_t,
                       int64_t *host_nb);
 
 /* Steps 1-5 only (debug/parity stage): writes the weighted series
- * wa = m a z e^{-2 pi i (f_h tau + fdot tau_b^2/2)} and wb (complex64,
+ * wa = m a z e^{-2 pi i (f_h tau + fdot tau_b^2/2 + fddot tau_b^3/6)} and wb (complex64,
  * interleaved re/im, [n_t][n_fft], zero beyond N_b) and abcd[n_t][4] =
  * (A, B, C, D) in float64.  x_h: complex64 [n_data] (8-byte aligned);
  * templates: device [n_t]; gaps: device int64 [2 * n_gaps_total]. */

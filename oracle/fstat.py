@@ -20,7 +20,7 @@ Readings of points the paper leaves open or garbles (each is pinned by a
   of the signal's spindown phase (Eq. 7 with Eq. 5);
 * Phi_s is the exact barycentric polynomial 2 pi sum_s f^(s) tau^(s+1)/(s+1)!
   with tau = t_b - t_start (Eq. 4 in barycentric time; Eq. 4pt1 is its
-  first-order expansion in t_m);
+  first-order expansion in t_m), here to s = 2 (fdot, fddot);
 * the heterodyne correction uses t_m at T^k, i.e. tau_k = t_b^k - T^k
   (Eq. phi-s-explain), applied after interpolating x_h (identical to the
   paper's order in the continuum);
@@ -49,6 +49,12 @@ def two_f(Fa, Fb, A, B, C, sigma2):
                   - 2.0 * C * np.real(Fa * np.conj(Fb))) / (sigma2 * D)
 
 
+def _fddot(tmpl):
+    """Second spindown of a template record (0 for records without it)."""
+    names = getattr(getattr(tmpl, "dtype", None), "names", None) or ()
+    return float(tmpl["fddot"]) if "fddot" in names else 0.0
+
+
 def _frac(x):
     return x - np.floor(x)
 
@@ -58,6 +64,7 @@ def resampled_series(x_h, tmpl, gaps, plan):
     the sums A, B, C.  Returns a dict with every intermediate."""
     a_, d_ = float(tmpl["alpha"]), float(tmpl["delta"])
     fdot = float(tmpl["fdot"])
+    fddot = _fddot(tmpl)
     tb, T, n_b = timemap.resample_times(tmpl, plan)
     u = resample.fractional_index(T, plan)
     valid = resample.valid_samples(plan.n_data, int(tmpl["span_start"]),
@@ -67,7 +74,7 @@ def resampled_series(x_h, tmpl, gaps, plan):
     tau = tb - T                                       # t_m(T^k), Eq. phi-s-explain
     tau_b = tb - plan.t_start
     # phase in cycles, reduced mod 1 before the complex exponential
-    cyc = _frac(plan.f_het * tau) + _frac(0.5 * fdot * tau_b * tau_b)
+    cyc = _frac(plan.f_het * tau) + _frac(0.5 * fdot * tau_b * tau_b) + _frac(fddot * tau_b ** 3 / 6.0)
     y = m * z * np.exp(-2j * np.pi * cyc)
     a, b = geometry.beam_ab(T, a_, d_, plan.det, plan.eph)
     return dict(tb=tb, T=T, u=u, m=m, z=z, y=y, a=a, b=b, n_b=n_b,
@@ -104,10 +111,11 @@ def bin_frequencies(n_fft, dt):
 def direct_two_f(x_h, tmpl, gaps, plan, df):
     """Direct demodulation (Eqs. 7-8 as sums over the valid detector samples):
     F_a(df) = sum_n a(t_n) x_h[n] exp(-2 pi i [f_h t_m(t_n) + df tau_n
-    + fdot tau_n^2 / 2]), tau_n = t_n - t_start + t_m(t_n); F_b alike; 2F as
-    in ``two_f``.  O(N) per frequency; no resampling."""
+    + fdot tau_n^2 / 2 + fddot tau_n^3 / 6]), tau_n = t_n - t_start + t_m(t_n);
+    F_b alike; 2F as in ``two_f``.  O(N) per frequency; no resampling."""
     a_, d_ = float(tmpl["alpha"]), float(tmpl["delta"])
     fdot = float(tmpl["fdot"])
+    fddot = _fddot(tmpl)
     valid = resample.valid_samples(plan.n_data, int(tmpl["span_start"]),
                                    int(tmpl["span_len"]), gaps)
     n = np.nonzero(valid)[0]
@@ -115,7 +123,7 @@ def direct_two_f(x_h, tmpl, gaps, plan, df):
     tm = geometry.roemer_delay(t, a_, d_, plan.det, plan.eph)
     tau = t - plan.t_start + tm
     a, b = geometry.beam_ab(t, a_, d_, plan.det, plan.eph)
-    cyc = _frac(plan.f_het * tm) + _frac(0.5 * fdot * tau * tau)
+    cyc = _frac(plan.f_het * tm) + _frac(0.5 * fdot * tau * tau) + _frac(fddot * tau ** 3 / 6.0)
     base = np.asarray(x_h, np.complex128)[n] * np.exp(-2j * np.pi * cyc)
     df = np.atleast_1d(np.asarray(df, dtype=np.float64))
     Fa = np.empty(df.size, np.complex128)

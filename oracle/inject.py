@@ -2,8 +2,8 @@
 
 Strain h = F_+ h_+ + F_x h_x (Eq. 1) with h_+ = A_+ cos Psi,
 h_x = A_x sin Psi, A_+ = h0 (1 + cos^2 iota)/2, A_x = h0 cos iota, and the
-phase Psi(t) = Phi_0 + 2 pi (f tau + fdot tau^2 / 2) with
-tau = t - t_start + t_m(t) (Eq. 4 with s = 1 written in barycentric time).
+phase Psi(t) = Phi_0 + 2 pi (f tau + fdot tau^2 / 2 + fddot tau^3 / 6) with
+tau = t - t_start + t_m(t) (Eq. 4 to s = 2 written in barycentric time).
 The detector series handed to the search is the heterodyned, band-limited
 complex series x_h = x exp(-2 pi i f_h (t - t_start)) (Sec. III.A.1); of the
 real signal only its positive-frequency half survives the low-pass, so
@@ -46,7 +46,8 @@ def signal(inj, plan, n_data=None, h0=None, valid=None):
     # Psi - 2 pi f_h (t - t_start) in cycles, reduced before exponentiation:
     # f tau - f_h (t - t_start) = f_h t_m + df tau
     cyc = (_frac(plan.f_het * tm) + _frac(inj.df * tau)
-           + _frac(0.5 * inj.fdot * tau * tau) + inj.phi0 / (2 * math.pi))
+           + _frac(0.5 * inj.fdot * tau * tau) + _frac(getattr(inj, "fddot", 0.0) * tau ** 3 / 6.0)
+           + inj.phi0 / (2 * math.pi))
     s = 0.5 * (Fp * Ap - 1j * Fx * Ax) * np.exp(2j * np.pi * _frac(cyc))
     if valid is not None:
         s = np.where(valid, s, 0.0)

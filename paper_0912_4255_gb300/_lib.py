@@ -46,7 +46,7 @@ class Template(ctypes.Structure):
     _fields_ = [("alpha", c_double), ("delta", c_double), ("fdot", c_double),
                 ("span_start", c_int64), ("span_len", c_int64),
                 ("gap_off", c_int64), ("n_gaps", c_int64),
-                ("n_fft", c_int64), ("out_off", c_int64)]
+                ("n_fft", c_int64), ("out_off", c_int64), ("fddot", c_double)]
 
 
 class Tuning(ctypes.Structure):

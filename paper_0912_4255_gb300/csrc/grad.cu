@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_adj(GradArgs<R> g) {
   const double fdt = df * pc.dt;
   const R Gar = (R)cot[0], Gai = (R)cot[1], Gbr = (R)cot[2], Gbi = (R)cot[3];
   const R gA = (R)cot[4], gB = (R)cot[5], gC = (R)cot[6];
-  const R dtr = (R)pc.dt, fh = (R)pc.f_het, fdot = (R)tp.fdot;
+  const R dtr = (R)pc.dt, fh = (R)pc.f_het, fdot = (R)tp.fdot, fddot = (R)tp.fddot;
   const R tb0r = (R)(m.tb0 - pc.t_start);
   const R rg0a = (R)g0a, rg0d = (R)g0d;
   const R rox = (R)ox, roy = (R)oy, roxa = (R)oxa, roya = (R)oya, roxd = (R)oxd, royd = (R)oyd;
@@ -355,8 +355,9 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_adj(GradArgs<R> g) {
     const double ck = fdt * (double)k;
     const R cyc = ph + (R)(ck - floor(ck)) + c0f;
     const C e = expm<R>(cyc);
-    const R dPa = fh * (rg0a - dTa) + (fdot * taub + (R)df) * rg0a;
-    const R dPd = fh * (rg0d - dTd) + (fdot * taub + (R)df) * rg0d;
+    const R fb = taub * (fdot + (R)0.5 * fddot * taub) + (R)df;   // d(Phi_s + df tau_b)/dt_b, cycles/s
+    const R dPa = fh * (rg0a - dTa) + fb * rg0a;
+    const R dPd = fh * (rg0d - dTd) + fb * rg0d;
     // y = z e, W_a = a y, W_b = b y
     const C y = cmul(z, e);
     const C dy = cmul(dz, e);

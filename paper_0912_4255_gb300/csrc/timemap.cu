@@ -2,7 +2,7 @@
 // uniform barycentric grid t_b^k = t_b(t_s) + k dt and, at knots every
 // h = 2^log2h grid points, the detector time T^k, the fractional data index
 // u = (T^k - t_start)/dt, the phase to remove
-// P = f_h t_m(T^k) + fdot tau_b^2 / 2 (cycles, Eq. absorb with
+// P = f_h t_m(T^k) + fdot tau_b^2 / 2 + fddot tau_b^3 / 6 (cycles, Eq. absorb with
 // Eq. phi-s-explain, tau_b = t_b - t_start) and the beam patterns a, b at
 // T^k (Eqs. 2-3), each with its derivative along the grid.  Consecutive
 // knots are joined by cubic Hermite pieces; the per-interval coefficients
@@ -26,7 +26,8 @@ struct KnotVal {
 };
 
 template <typename R>
-__device__ KnotVal<R> knot_value(const PlanConst& pc, const Sky<R>& sky, double tb0, int64_t k, R fdot) {
+__device__ KnotVal<R> knot_value(const PlanConst& pc, const Sky<R>& sky, double tb0, int64_t k, R fdot,
+                                 R fddot) {
   KnotVal<R> v;
   const R tb = (R)(tb0 + (double)k * pc.dt);
   R tm, rate, sH, cH, inv1r;
@@ -35,8 +36,9 @@ __device__ KnotVal<R> knot_value(const PlanConst& pc, const Sky<R>& sky, double 
   v.U = (T - (R)pc.t_start) * (R)pc.inv_dt;
   v.dU = inv1r;
   const R taub = tb - (R)pc.t_start;
-  v.P = (R)pc.f_het * tm + (R)0.5 * fdot * taub * taub;
-  v.dP = (R)pc.f_het * rate * dTdk + fdot * taub * (R)pc.dt;
+  // spindown phase of Eq. 4 to s = 2 in barycentric time, and its rate
+  v.P = (R)pc.f_het * tm + taub * taub * ((R)0.5 * fdot + fddot * taub * (R)(1.0 / 6));
+  v.dP = (R)pc.f_het * rate * dTdk + taub * (fdot + (R)0.5 * fddot * taub) * (R)pc.dt;
   R a, b, da, db;
   beams_h<R>(pc, sky, sH, cH, &a, &b, &da, &db);
   v.a = a; v.b = b; v.da = da * dTdk; v.db = db * dTdk;
@@ -135,7 +137,8 @@ k_timemap(PlanConst pc, const fstat_template* __restrict__ tmpl, TmplMeta* __res
   // --- per-template grid and validation (every block computes the same)
   int st = FSTAT_OK;
   const int64_t n_data = pc.n_data;
-  if (!(isfinite(tp.alpha) && isfinite(tp.delta) && isfinite(tp.fdot)) || fabs(tp.delta) > 1.5707963267948967)
+  if (!(isfinite(tp.alpha) && isfinite(tp.delta) && isfinite(tp.fdot) && isfinite(tp.fddot)) ||
+      fabs(tp.delta) > 1.5707963267948967)
     st = FSTAT_EINVAL;
   if (tp.span_start < 0 || tp.span_len < 2 || tp.span_start + tp.span_len > n_data) st = FSTAT_ERANGE;
   if (tp.n_gaps < 0 || tp.gap_off < 0 || tp.gap_off + tp.n_gaps > n_gaps_total) st = FSTAT_EINVAL;
@@ -201,9 +204,10 @@ k_timemap(PlanConst pc, const fstat_template* __restrict__ tmpl, TmplMeta* __res
   if (j0 > n_int) return;
   const Sky<RK> sky = make_sky<RK>(pc, (RK)tp.alpha, (RK)tp.delta);
   const int64_t j = j0 + threadIdx.x;
-  if (j <= n_int) kv[threadIdx.x] = knot_value<RK>(pc, sky, tb0, j << pc.log2h, (RK)tp.fdot);
+  if (j <= n_int) kv[threadIdx.x] = knot_value<RK>(pc, sky, tb0, j << pc.log2h, (RK)tp.fdot, (RK)tp.fddot);
   if (threadIdx.x == 0 && j0 + kKnotThreads <= n_int)
-    kv[kKnotThreads] = knot_value<RK>(pc, sky, tb0, (j0 + kKnotThreads) << pc.log2h, (RK)tp.fdot);
+    kv[kKnotThreads] = knot_value<RK>(pc, sky, tb0, (j0 + kKnotThreads) << pc.log2h, (RK)tp.fdot,
+                                      (RK)tp.fddot);
   __syncthreads();
   if (j < n_int) write_record(knots + (int64_t)t * knot_stride + j, kv[threadIdx.x], kv[threadIdx.x + 1], (RK)h);
 }

@@ -94,15 +94,16 @@ TEMPLATE_DTYPE = np.dtype([
     ("span_start", np.int64), ("span_len", np.int64),
     ("gap_off", np.int64), ("n_gaps", np.int64),
     ("n_fft", np.int64), ("out_off", np.int64),
+    ("fddot", np.float64),
 ])
 
 
 def make_templates(alpha, delta, fdot, span_start=0, span_len=None, gap_off=0,
-                   n_gaps=0, n_fft=0, out_off=-1, n_data=None) -> np.ndarray:
+                   n_gaps=0, n_fft=0, out_off=-1, n_data=None, fddot=0.0) -> np.ndarray:
     """Pack per-template parameters (broadcast) into a TEMPLATE_DTYPE array.
 
     ``n_fft = 0`` means "the plan's n_fft"; ``out_off = -1`` means
-    ``index * n_fft``.
+    ``index * n_fft``; ``fddot`` is the second spindown.
     """
     alpha = np.atleast_1d(np.asarray(alpha, dtype=np.float64))
     n = alpha.size
@@ -120,6 +121,7 @@ def make_templates(alpha, delta, fdot, span_start=0, span_len=None, gap_off=0,
     t["n_gaps"] = np.broadcast_to(np.asarray(n_gaps, np.int64), (n,))
     t["n_fft"] = np.broadcast_to(np.asarray(n_fft, np.int64), (n,))
     t["out_off"] = np.broadcast_to(np.asarray(out_off, np.int64), (n,))
+    t["fddot"] = np.broadcast_to(np.asarray(fddot, np.float64), (n,))
     return t
 
 
@@ -201,7 +203,7 @@ class Injection:
     """Amplitude and Doppler parameters of one injected signal: strain
     amplitude h0 (or target SNR rho), inclination cos(iota), polarisation
     psi, initial phase phi0, sky (alpha, delta), frequency offset df above
-    the heterodyne frequency and spindown fdot."""
+    the heterodyne frequency, spindown fdot and second spindown fddot."""
     alpha: float
     delta: float
     df: float
@@ -211,10 +213,12 @@ class Injection:
     phi0: float
     rho: float = 20.0
     h0: float | None = None
+    fddot: float = 0.0
 
 
 def random_injection(seed: int, df: float, fdot: float = 0.0, rho: float = 20.0,
-                     alpha: float | None = None, delta: float | None = None) -> Injection:
+                     alpha: float | None = None, delta: float | None = None,
+                     fddot: float = 0.0) -> Injection:
     g = rng(seed)
     a = g.uniform(0.0, 2.0 * math.pi) if alpha is None else alpha
     d = math.asin(g.uniform(-1.0, 1.0)) if delta is None else delta
@@ -222,7 +226,7 @@ def random_injection(seed: int, df: float, fdot: float = 0.0, rho: float = 20.0,
     cosi = g.uniform(-1.0, 1.0)
     phi0 = g.uniform(0.0, 2.0 * math.pi)
     return Injection(alpha=a, delta=d, df=df, fdot=fdot, psi=psi, cosi=cosi,
-                     phi0=phi0, rho=rho)
+                     phi0=phi0, rho=rho, fddot=fddot)
 
 
 def next_pow2(n: int) -> int:

@@ -66,6 +66,28 @@ def test_adjoint_matches_fp64_central_differences():
         assert err < 1e-3, (i, grad[i], ref)
 
 
+def test_adjoint_with_second_spindown():
+    """The adjoint's phase rate includes the second spindown: gradient
+    against the oracle's central differences for templates with fddot."""
+    d, gaps, injs, x = _setup(100_000, 57, n_inj=1)
+    T = d.n_data * d.dt
+    inj = injs[0]
+    tm = synth.make_templates([inj.alpha, inj.alpha + 1e-3], [inj.delta, inj.delta - 1e-3],
+                              [inj.fdot, inj.fdot + 0.2 / T ** 2], 0, d.n_data, 0, len(gaps),
+                              fddot=[2e-14, -3e-14])
+    df = np.array([inj.df, inj.df + 0.1 / T])
+    (two_f, grad), rc = _grad_gpu(d, x, tm, df, gaps)
+    assert rc == 0
+    xc = x.astype(np.complex128)
+    scale = np.array([1e-3, 1e-3, 1.0 / T, 1.0 / T ** 2])
+    for i in range(2):
+        ref2f = F.single_bin_two_f(xc, tm[i], gaps, d, df[i])
+        assert abs(two_f[i] - ref2f) / max(ref2f, 4.0) < 1e-4
+        ref = F.single_bin_gradient(xc, tm[i], gaps, d, df[i])
+        err = np.linalg.norm((grad[i] - ref) * scale) / max(np.linalg.norm(ref * scale), 1e-3 * max(ref2f, 4.0))
+        assert err < 1e-3, (i, grad[i], ref)
+
+
 def test_autograd_function_backward():
     import torch
     import paper_0912_4255_gb300 as fs

@@ -138,6 +138,24 @@ def test_fp64_mode_tight(mode):
         assert r15(got[i], oracle_two_f(d, x, tm[i])) <= 1e-6
 
 
+def test_second_spindown_against_oracle():
+    """Templates with a second spindown (Eq. 4 to s = 2): the knots carry
+    fddot tau^3 / 6 in the phase; 2F in every bin against the oracle, and
+    the injection recovered only with its own fddot."""
+    d = synth.PlanDesc(dt=0.5, n_data=300_000, n_fft=1 << 19, interp=R.SINC, f_het=110.0,
+                       max_templates=3)
+    inj = synth.random_injection(81, df=0.2, fdot=-2e-9, fddot=1e-14)   # 5.6 cycles over the span
+    x, info = injected_series(d, 82, [inj])
+    tm = synth.make_templates([inj.alpha] * 3, inj.delta, inj.fdot, 0, d.n_data,
+                              fddot=[inj.fddot, 0.0, -inj.fddot])
+    got, rc = run_compute(d, x, tm)
+    assert rc == 0
+    refs = [oracle_two_f(d, x, tm[i]) for i in range(3)]
+    for i in range(3):
+        assert r15(got[i], refs[i]) <= TOL, i
+    assert np.max(got[0]) > 2 * np.max(got[1])
+
+
 @pytest.mark.parametrize("mode", ["fused", "split"])
 def test_invalid_template_reports_status_and_nan(mode):
     import paper_0912_4255_gb300 as fs

@@ -277,6 +277,24 @@ def test_spindown_and_heterodyne_signs():
     assert np.max(rb) < 0.2 * info[0][1]
 
 
+def test_second_spindown_phase():
+    """Eq. 4 to s = 2: a signal with a second spindown is recovered to
+    rho^2 (noise-free direct demodulation) only by the template with the
+    same fddot; without it, or with the opposite sign, the phase runs
+    ~10 cycles off over the span and the power is lost."""
+    plan = synth.PlanDesc(dt=0.5, n_data=4 * 86400 * 2, n_fft=1 << 20, f_het=150.0, interp=R.SINC)
+    valid = I.valid_all(plan)
+    inj = synth.random_injection(14, df=0.125, fdot=-3e-10, fddot=4e-16)
+    x, info = I.inject(np.zeros(plan.n_data), [inj], plan, valid)
+    rho2 = info[0][1]
+    got = {}
+    for name, fdd in (("same", inj.fddot), ("none", 0.0), ("flip", -inj.fddot)):
+        t = synth.make_templates(inj.alpha, inj.delta, inj.fdot, 0, plan.n_data, fddot=fdd)[0]
+        got[name] = float(F.direct_two_f(x, t, NOGAPS, plan, inj.df)[0])
+    assert abs(got["same"] - rho2) / rho2 < 1e-9
+    assert got["none"] < 0.3 * rho2 and got["flip"] < 0.3 * rho2
+
+
 def test_nearest_neighbour_loss_is_sinc_squared():
     """Sec. V.B: interpolation loses power towards the band edge (of order
     30 %).  For nearest-neighbour resampling with rounding errors spread
