@@ -264,9 +264,12 @@ def main():
                     help="log2 of the first-pass FFT length (0: the library's default)")
     ap.add_argument("--copy-streams", type=int, default=4,
                     help="streams the end-to-end leg splits each batch's device-to-host copy over")
-    ap.add_argument("--workload", default="search", choices=["search", "batch"],
+    ap.add_argument("--workload", default="search", choices=["search", "batch", "montecarlo"],
                     help="search: the 8192-template grid (the metric's workload); batch: 4096 "
-                         "templates with uneven spans, own gap lists and FFT lengths")
+                         "templates with uneven spans, own gap lists and FFT lengths; montecarlo: "
+                         "noise-only realizations of the 12 h nearest-neighbour configuration")
+    ap.add_argument("--realizations", type=int, default=1 << 20,
+                    help="Monte Carlo realizations (--workload montecarlo)")
     ap.add_argument("--topk", type=int, default=16,
                     help="candidates per band for the e2e_candidates leg (0: skip it)")
     ap.add_argument("--topk-band", type=int, default=65536, help="bins per candidate band")
@@ -282,6 +285,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "montecarlo":
+        return run_montecarlo(args)
 
     import torch
     import torch.distributed as dist
@@ -540,6 +545,69 @@ def run_e2e_candidates(fs, plan, desc, x_np, tm, gaps_np, dev, args, world, batc
             "h2d_bytes_per_step": int(x_h.numel() * 8 + g_h.numel() * 8 + t_h.numel()),
             "d2h_bytes_per_step": int(hv.numel() * 4 + hb.numel() * 4),
             "ms_per_step": wall * 1e3, "steps": steps, "band_len": band_len, "k": k}
+
+
+def run_montecarlo(args):
+    """The paper's validation at its scale (Sec. IV.B: 2F is chi^2_4 in
+    Gaussian noise): R noise-only realizations of the 12 h configuration
+    (86,400 samples, nearest neighbour, FFT 2^17), 4096 per call as
+    consecutive spans of one series (one template per span), Gaussian noise
+    drawn on the GPU from a seeded generator; reports the mean and variance
+    of 2F and its tail probabilities against chi^2_4's closed forms, and the
+    rate (noise generation included)."""
+    import torch
+    import paper_0912_4255_gb300 as fs
+    from paper_0912_4255_gb300 import build as fsbuild
+    fsbuild.build()
+    dev = torch.device("cuda", 0)
+    span, per = 86400, 4096
+    total = max(per, (args.realizations // per) * per)
+    desc = synth.tiny_plan(n_data=span * per, max_templates=per)
+    plan = fs.Plan(desc, device=dev)
+    a, d = synth.random_sky(1, synth.SEED_BASE + 33)
+    tm = fs.pack_templates(synth.make_templates(np.repeat(a, per), float(d[0]), 0.0,
+                                                np.arange(per) * span, span), device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(synth.SEED_BASE + 34)
+    raw = torch.empty(2 * span * per, dtype=torch.float32, device=dev)
+    x = raw.view(torch.complex64)
+    out = torch.empty(per * desc.n_fft, dtype=torch.float32, device=dev)
+    thr = (10.0, 20.0, 30.0)
+    acc = torch.zeros(5, dtype=torch.float64, device=dev)     # sum, sum of squares, tail counts
+    scale = math.sqrt(desc.sigma2 / 2.0)
+
+    def batch():
+        torch.randn(raw.shape, generator=gen, device=dev, out=raw)
+        raw.mul_(scale)
+        fs.fstat_compute(plan, x, tm, None, out)
+        acc[0] += out.sum(dtype=torch.float64)
+        acc[1] += out.square().sum(dtype=torch.float64)
+        for i in range(3):
+            acc[2 + i] += (out > thr[i]).sum()
+
+    batch()                                   # warm-up (not counted)
+    torch.cuda.synchronize(dev)
+    acc.zero_()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(total // per):
+        batch()
+    ev1.record()
+    torch.cuda.synchronize(dev)
+    rc = fs.fstat_status(plan, raise_error=False)
+    ms = ev0.elapsed_time(ev1)
+    n = float(total) * desc.n_fft
+    mean = float(acc[0]) / n
+    var = float(acc[1]) / n - mean * mean
+    tails = {f"P(2F>{int(t)})": {"measured": float(acc[2 + i]) / n,
+                                 "chi2_4": math.exp(-t / 2) * (1 + t / 2)}
+             for i, t in enumerate((10.0, 20.0, 30.0))}
+    print(json.dumps({
+        "workload": "montecarlo", "realizations": total, "bins_per_realization": int(desc.n_fft),
+        "two_f_values": n, "ms": ms, "two_f_values_per_s": n / (ms / 1e3),
+        "config": "12 h at dt = 0.5 s (86,400 samples), nearest neighbour, FFT 2^17, noise only, "
+                  "4096 realizations per call, noise drawn on the GPU",
+        "mean": mean, "var": var, "chi2_4": {"mean": 4.0, "var": 8.0}, "tails": tails, "status": rc}))
 
 
 def run_batch(args):
