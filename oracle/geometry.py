@@ -127,11 +127,14 @@ def detector_tensor(t, det, eph):
 
 def polarisation_tensors(alpha, delta, psi=0.0):
     """eps_+ and eps_x for a wave from direction n0(alpha, delta), in the
-    basis (e_alpha, e_delta) rotated by the polarisation angle psi."""
+    basis (e_alpha, -e_delta) rotated by the polarisation angle psi.  The
+    orientation of the basis (the sign of eps_x) and the sense of psi are
+    the ones of Eqs. 2-3: with them d : eps_+ = a cos 2psi + b sin 2psi and
+    d : eps_x = b cos 2psi - a sin 2psi for the JKS a, b."""
     ea = np.array([-np.sin(alpha), np.cos(alpha), 0.0])
     ed = np.array([-np.sin(delta) * np.cos(alpha), -np.sin(delta) * np.sin(alpha), np.cos(delta)])
     ep = np.outer(ea, ea) - np.outer(ed, ed)
-    ex = np.outer(ea, ed) + np.outer(ed, ea)
+    ex = -(np.outer(ea, ed) + np.outer(ed, ea))
     c, s = np.cos(2 * psi), np.sin(2 * psi)
     return c * ep + s * ex, -s * ep + c * ex
 

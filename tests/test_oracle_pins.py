@@ -55,6 +55,26 @@ def test_beam_closed_form_is_tensor_form_up_to_orthogonal_map(seed):
     assert np.allclose(M.T @ M, np.eye(2), atol=1e-12)
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_antenna_functions_follow_eqs_2_3(seed):
+    """Eqs. 2-3 with zeta = 90 deg: F_+ = a cos 2psi + b sin 2psi and
+    F_x = b cos 2psi - a sin 2psi, the tensor contraction against the JKS
+    closed form at several polarisation angles (a flipped sign of eps_x or of
+    psi fails here)."""
+    g = synth.rng(seed)
+    det = synth.Detector(lat_rad=g.uniform(-1.4, 1.4), lon_rad=g.uniform(-3, 3),
+                         gamma_rad=g.uniform(0, math.pi))
+    plan = synth.PlanDesc(det=det)
+    alpha, delta = g.uniform(0, 2 * math.pi), math.asin(g.uniform(-1, 1))
+    t = np.linspace(0, 86400, 501)
+    a, b = G.beam_ab(t, alpha, delta, plan.det, plan.eph)
+    for psi in (0.0, 0.3, 1.2, 2.9):
+        c, s = math.cos(2 * psi), math.sin(2 * psi)
+        fp, fx = G.antenna_tensor(t, alpha, delta, psi, plan.det, plan.eph)
+        assert np.max(np.abs(fp - (a * c + b * s))) < 1e-12
+        assert np.max(np.abs(fx - (b * c - a * s))) < 1e-12
+
+
 def test_beam_zenith_unit_response():
     """Sec. II after Eq. 3 (zeta = 90 deg): for a source at the zenith the
     response to an optimally oriented wave is 1, i.e. a^2 + b^2 = 1."""
