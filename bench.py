@@ -269,7 +269,9 @@ def main():
                          "templates with uneven spans, own gap lists and FFT lengths; montecarlo: "
                          "noise-only realizations of the 12 h nearest-neighbour configuration")
     ap.add_argument("--realizations", type=int, default=1 << 20,
-                    help="Monte Carlo realizations (--workload montecarlo)")
+                    help="Monte Carlo realizations (--workload montecarlo), noise only and with signals")
+    ap.add_argument("--mc-h0", type=float, default=0.12,
+                    help="injected amplitude of the Monte Carlo with signals (sigma^2 = 1; mean rho^2 ~ 100)")
     ap.add_argument("--topk", type=int, default=16,
                     help="candidates per band for the e2e_candidates leg (0: skip it)")
     ap.add_argument("--topk-band", type=int, default=65536, help="bins per candidate band")
@@ -549,12 +551,14 @@ def run_e2e_candidates(fs, plan, desc, x_np, tm, gaps_np, dev, args, world, batc
 
 def run_montecarlo(args):
     """The paper's validation at its scale (Sec. IV.B: 2F is chi^2_4 in
-    Gaussian noise): R noise-only realizations of the 12 h configuration
-    (86,400 samples, nearest neighbour, FFT 2^17), 4096 per call as
-    consecutive spans of one series (one template per span), Gaussian noise
-    drawn on the GPU from a seeded generator; reports the mean and variance
-    of 2F and its tail probabilities against chi^2_4's closed forms, and the
-    rate (noise generation included)."""
+    Gaussian noise, non-central chi^2_4 with a signal): R noise-only
+    realizations of the 12 h configuration (86,400 samples, nearest
+    neighbour, FFT 2^17), 4096 per call as consecutive spans of one series
+    (one template per span), Gaussian noise drawn on the GPU from a seeded
+    generator; reports the mean and variance of 2F and its tail
+    probabilities against chi^2_4's closed forms and the rate (noise
+    generation included); then R realizations with one injected signal
+    each, standardized against the non-central chi^2_4."""
     import torch
     import paper_0912_4255_gb300 as fs
     from paper_0912_4255_gb300 import build as fsbuild
@@ -602,12 +606,68 @@ def run_montecarlo(args):
     tails = {f"P(2F>{int(t)})": {"measured": float(acc[2 + i]) / n,
                                  "chi2_4": math.exp(-t / 2) * (1 + t / 2)}
              for i, t in enumerate((10.0, 20.0, 30.0))}
+    noise_only = {"realizations": total, "two_f_values": n, "ms": ms, "two_f_values_per_s": n / (ms / 1e3),
+                  "mean": mean, "var": var, "chi2_4": {"mean": 4.0, "var": 8.0}, "tails": tails}
+
+    # --- with signals: every realization carries one injection (isotropic
+    # sky and orientation, h0 = args.mc_h0, frequency on bin q) added on the
+    # GPU by fstat_inject and searched with its own template; the expected
+    # non-centrality lambda is 2F of the noise-free injection at bin q
+    # (resampling loss included), and z = (2F - lambda - 4) / sqrt(8 + 4 lambda)
+    # has mean 0 and variance 1 for a non-central chi^2_4.
+    q_off = 3000
+    q = desc.n_fft // 2 + q_off
+    df = q_off / (desc.n_fft * desc.dt)
+    n_b = total // per
+    recs = [synth.random_injection_records(per, synth.SEED_BASE + 1000 + b, df, args.mc_h0, span)
+            for b in range(n_b)]
+    inj_dev = torch.cat([fs.pack_injections(r, device=None)[0] for r in recs]).to(dev)
+    tm_dev = torch.cat([fs.pack_templates(synth.make_templates(r["alpha"], r["delta"], 0.0, r["span_start"],
+                                                               span), device=None) for r in recs]).to(dev)
+    ib, tb = fs.INJECTION_DTYPE.itemsize * per, synth.TEMPLATE_DTYPE.itemsize * per
+    sig = torch.empty(span * per, dtype=torch.complex64, device=dev)
+    acc2 = torch.zeros(5, dtype=torch.float64, device=dev)   # sum z, sum z^2, sum (2F - 4), sum lambda, n(lambda > 0)
+
+    def sbatch(b):
+        rb, tmb = inj_dev[b * ib:(b + 1) * ib], tm_dev[b * tb:(b + 1) * tb]
+        sig.zero_()
+        fs.fstat_inject(plan, sig, rb, span)
+        fs.fstat_compute(plan, sig, tmb, None, out)
+        lam = out.view(per, -1)[:, q].double()
+        torch.randn(raw.shape, generator=gen, device=dev, out=raw)
+        raw.mul_(scale)
+        fs.fstat_inject(plan, x, rb, span)
+        fs.fstat_compute(plan, x, tmb, None, out)
+        f = out.view(per, -1)[:, q].double()
+        z = (f - lam - 4.0) / torch.sqrt(8.0 + 4.0 * lam)
+        acc2[0] += z.sum()
+        acc2[1] += (z * z).sum()
+        acc2[2] += (f - 4.0).sum()
+        acc2[3] += lam.sum()
+        acc2[4] += (lam > 0).sum()
+
+    sbatch(0)                                 # warm-up (not counted)
+    torch.cuda.synchronize(dev)
+    acc2.zero_()
+    ev0.record()
+    for b in range(n_b):
+        sbatch(b)
+    ev1.record()
+    torch.cuda.synchronize(dev)
+    rc = rc or fs.fstat_status(plan, raise_error=False)
+    ms2 = ev0.elapsed_time(ev1)
+    zm = float(acc2[0]) / total
+    with_signal = {"realizations": total, "h0": args.mc_h0, "bin": q_off, "ms": ms2,
+                   "mean_lambda": float(acc2[3]) / total,
+                   "z_mean": zm, "z_var": float(acc2[1]) / total - zm * zm,
+                   "sum_2F_minus_4_over_sum_lambda": float(acc2[2]) / float(acc2[3]),
+                   "expected": {"z_mean": 0.0, "z_var": 1.0, "ratio": 1.0}}
     print(json.dumps({
-        "workload": "montecarlo", "realizations": total, "bins_per_realization": int(desc.n_fft),
-        "two_f_values": n, "ms": ms, "two_f_values_per_s": n / (ms / 1e3),
-        "config": "12 h at dt = 0.5 s (86,400 samples), nearest neighbour, FFT 2^17, noise only, "
-                  "4096 realizations per call, noise drawn on the GPU",
-        "mean": mean, "var": var, "chi2_4": {"mean": 4.0, "var": 8.0}, "tails": tails, "status": rc}))
+        "workload": "montecarlo",
+        "config": "12 h at dt = 0.5 s (86,400 samples), nearest neighbour, FFT 2^17, 4096 realizations "
+                  "per call as consecutive spans of one series, noise drawn on the GPU; with signals: "
+                  "injections by fstat_inject, lambda from the noise-free run",
+        "noise_only": noise_only, "with_signal": with_signal, "status": rc}))
 
 
 def run_batch(args):

@@ -132,6 +132,21 @@ typedef struct fstat_template {
   double fddot;
 } fstat_template;
 
+/* One injected signal (Eqs. 1-4, the signal model the statistic detects):
+ * strain h = F_+ A_+ cos Psi + F_x A_x sin Psi with A_+ = h0 (1 + cosi^2)/2,
+ * A_x = h0 cosi, F_+ = a cos 2psi + b sin 2psi, F_x = b cos 2psi - a sin 2psi
+ * (a, b of Eqs. 2-3 at the detector), and the phase
+ * Psi = phi0 + 2 pi [(f_het + df) tau + fdot tau^2 / 2 + fddot tau^3 / 6],
+ * tau = t - t_start + t_m(t) (Eq. 4 to s = 2, t_m the Roemer delay of
+ * Eq. 4pt2 for the sky position alpha, delta).  Angles in radians, df in Hz
+ * above f_het, spindowns in Hz/s and Hz/s^2; added to the data samples
+ * [span_start, span_start + span_len). */
+typedef struct fstat_injection {
+  double alpha, delta, psi, cosi, phi0, h0;
+  double df, fdot, fddot;
+  int64_t span_start, span_len;
+} fstat_injection;
+
 /* Kernel shape choices (set by the autotuner; zeros mean automatic).
  * log2_n1: log2 of the first-pass (column) FFT length; cols: columns per
  * block in the first pass; rows: rows per block in the second pass; chunk:
@@ -254,6 +269,27 @@ int fstat_compute_noalloc(const fstat_plan_desc *d, const float *x_h, const fsta
  * stream; needs no plan. */
 int fstat_topk(const float *twoF, int64_t n_rows, int64_t row_len, int64_t band_len, int k,
                float *val, int32_t *bin, void *stream);
+
+/* Signal injection for Monte Carlo studies (Sec. IV.B: 2F of data holding
+ * a signal is non-central chi^2 with 4 degrees of freedom): adds to x_h, the
+ * heterodyned complex series of the plan (complex64 [n_data], device,
+ * 8-byte aligned), the heterodyned positive-frequency half of each
+ * injection's strain over its span,
+ *   x_h[n] += 1/2 (F_+ A_+ - i F_x A_x) exp(i [Psi(t_n) - 2 pi f_het (t_n - t_start)]),
+ * t_n = t_start + n dt.  Gaps are not applied (the search masks them).
+ * injections: device array of n_inj records; max_span_len: an upper bound
+ * of their span_len (it sizes the grid).  A record with a non-finite
+ * parameter, |delta| > pi/2, or a span outside [0, n_data) or longer than
+ * max_span_len is skipped and sets the plan's status (EINVAL / ERANGE,
+ * read by fstat_status).  Injections whose spans overlap are summed with
+ * atomic adds (the order of their additions is unspecified); disjoint spans
+ * give one rounding per sample.  The detector response and phase are
+ * evaluated in FP64 at knots every 1024 samples and joined by cubic Hermite
+ * pieces, as in the time map.  Host errors: EINVAL (null or misaligned
+ * pointer, n_inj < 0, max_span_len < 0), ERANGE (max_span_len above 2^41
+ * samples), ECUDA.  Asynchronous on stream. */
+int fstat_inject(fstat_plan_t p, const fstat_injection *injections, int64_t n_inj,
+                 int64_t max_span_len, float *x_h, void *stream);
 
 /* Synchronise the stream, return and clear the first device-side error
  * recorded since the last call (FSTAT_OK if none). */

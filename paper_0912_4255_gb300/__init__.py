@@ -17,14 +17,15 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (MODE_FUSED, MODE_PERSISTENT, MODE_PLAIN, MODE_SPLIT, NEAREST, PREC_FP32, PREC_FP64,
-                   PREC_MIXED, SINC, TEMPLATE_DTYPE, WIN_LANCZOS, WIN_RECT)
+from ._lib import (INJECTION_DTYPE, MODE_FUSED, MODE_PERSISTENT, MODE_PLAIN, MODE_SPLIT, NEAREST, PREC_FP32,
+                   PREC_FP64, PREC_MIXED, SINC, TEMPLATE_DTYPE, WIN_LANCZOS, WIN_RECT)
 
 __all__ = [
     "FstatError", "Plan", "fstat_plan", "fstat_compute", "fstat_compute_noalloc", "fstat_resample",
     "fstat_grad",
     "fstat_status", "fstat_destroy", "fstat_strerror", "fstat_template_nb", "pack_templates",
     "fstat_profile", "fstat_profile_read", "KERNEL_KINDS", "GraphRunner", "fstat_debug_stall", "fstat_topk",
+    "fstat_inject", "pack_injections", "INJECTION_DTYPE",
     "NEAREST", "SINC", "WIN_RECT", "WIN_LANCZOS", "PREC_MIXED", "PREC_FP64", "PREC_FP32",
     "MODE_FUSED", "MODE_PLAIN", "MODE_PERSISTENT", "MODE_SPLIT", "TEMPLATE_DTYPE",
 ]
@@ -82,6 +83,19 @@ def pack_templates(templates, device="cuda"):
             arr[name] = [t.get(name, -1 if name == "out_off" else 0) for t in templates]
     raw = torch.from_numpy(arr.view(np.uint8).copy())
     return raw.to(device) if device is not None else raw
+
+
+def pack_injections(injections, device="cuda"):
+    """Upload injections (a structured array with the fstat_injection
+    fields) as a device tensor of raw fstat_injection records; returns
+    (records, the longest span_len)."""
+    import torch
+    arr = np.zeros(len(injections), dtype=INJECTION_DTYPE)
+    for name in INJECTION_DTYPE.names:
+        arr[name] = injections[name]
+    raw = torch.from_numpy(arr.view(np.uint8).copy())
+    longest = int(arr["span_len"].max()) if len(arr) else 0
+    return (raw.to(device) if device is not None else raw), longest
 
 
 class Plan:
@@ -214,6 +228,23 @@ def fstat_grad(plan: Plan, x_h, templates, df, gaps=None, stream=None):
 
 
 KERNEL_KINDS = ("timemap", "resample", "fft_cols", "fft_rows", "grad_fwd", "grad_adj", "persistent", "sums")
+
+
+def fstat_inject(plan: Plan, x_h, injections, max_span_len: int | None = None, stream=None):
+    """Add the injections' signals to x_h (device complex64, in place).
+    ``injections``: a structured array with the fstat_injection fields, or
+    device records from ``pack_injections`` together with ``max_span_len``."""
+    import torch
+    assert x_h.is_cuda and x_h.dtype == torch.complex64 and x_h.is_contiguous()
+    if isinstance(injections, np.ndarray):
+        injections, longest = pack_injections(injections, device=x_h.device)
+        max_span_len = longest if max_span_len is None else max_span_len
+    if max_span_len is None:
+        raise ValueError("max_span_len is needed with device records")
+    n = injections.numel() // INJECTION_DTYPE.itemsize
+    _check(plan.lib.fstat_inject(plan.handle, _ptr(injections), n, int(max_span_len), _ptr(x_h),
+                                 _stream(stream)), "fstat_inject")
+    return x_h
 
 
 def fstat_topk(two_f, band_len: int, k: int, n_rows: int | None = None, stream=None):

@@ -49,6 +49,12 @@ class Template(ctypes.Structure):
                 ("n_fft", c_int64), ("out_off", c_int64), ("fddot", c_double)]
 
 
+class Injection(ctypes.Structure):
+    _fields_ = [("alpha", c_double), ("delta", c_double), ("psi", c_double), ("cosi", c_double),
+                ("phi0", c_double), ("h0", c_double), ("df", c_double), ("fdot", c_double),
+                ("fddot", c_double), ("span_start", c_int64), ("span_len", c_int64)]
+
+
 class Tuning(ctypes.Structure):
     _fields_ = [("mode", c_int32), ("log2_n1", c_int32), ("cols", c_int32),
                 ("rows", c_int32), ("chunk", c_int32), ("knot_log2", c_int32)]
@@ -58,6 +64,10 @@ class Tuning(ctypes.Structure):
 TEMPLATE_DTYPE = np.dtype([(n, np.float64 if t is c_double else np.int64)
                            for n, t in Template._fields_])
 assert TEMPLATE_DTYPE.itemsize == ctypes.sizeof(Template)
+# numpy view of fstat_injection
+INJECTION_DTYPE = np.dtype([(n, np.float64 if t is c_double else np.int64)
+                            for n, t in Injection._fields_])
+assert INJECTION_DTYPE.itemsize == ctypes.sizeof(Injection)
 
 SYMBOLS = {
     "fstat_plan": (ctypes.c_int, [ctypes.POINTER(c_void_p), ctypes.POINTER(PlanDesc),
@@ -78,6 +88,7 @@ SYMBOLS = {
     "fstat_debug_stall": (ctypes.c_int, [c_void_p, c_int64]),
     "fstat_topk": (ctypes.c_int, [c_void_p, c_int64, c_int64, c_int64, ctypes.c_int, c_void_p, c_void_p,
                                   c_void_p]),
+    "fstat_inject": (ctypes.c_int, [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_void_p]),
     "fstat_profile": (ctypes.c_int, [c_void_p, ctypes.c_int]),
     "fstat_profile_read": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int64),
                                           ctypes.c_int]),

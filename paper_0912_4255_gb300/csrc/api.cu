@@ -485,6 +485,17 @@ int fstat_profile_read(fstat_plan_t p, double* ms, int64_t* launches, int n_kind
   return rc;
 }
 
+int fstat_inject(fstat_plan_t p, const fstat_injection* inj, int64_t n_inj, int64_t max_span_len, float* x_h,
+                 void* stream) {
+  if (!p || !x_h || ((uintptr_t)x_h & 7) || n_inj < 0 || max_span_len < 0 || (n_inj > 0 && !inj))
+    return FSTAT_EINVAL;
+  if (n_inj == 0 || max_span_len == 0) return FSTAT_OK;
+  const cudaError_t e = launch_inject(p->pc, inj, n_inj, max_span_len, reinterpret_cast<float2*>(x_h), p->status,
+                                      static_cast<cudaStream_t>(stream));
+  if (e == cudaErrorInvalidValue) return FSTAT_ERANGE;
+  return e == cudaSuccess ? FSTAT_OK : FSTAT_ECUDA;
+}
+
 int fstat_status(fstat_plan_t p, void* stream) {
   if (!p) return FSTAT_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

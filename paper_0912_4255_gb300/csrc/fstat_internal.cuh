@@ -942,6 +942,8 @@ __host__ __device__ inline int default_log2_n1(int L) {
   return l1;
 }
 
+cudaError_t launch_inject(const PlanConst& pc, const fstat_injection* inj, int64_t n_inj, int64_t max_span,
+                          float2* x, int* status, cudaStream_t s);
 cudaError_t launch_timemap(const PlanConst& pc, const Chunk& c, int log2n_plan, int mode,
                            const int64_t* gaps, int64_t n_gaps_total, int* status,
                            int64_t tmpl_base, cudaStream_t s);

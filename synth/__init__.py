@@ -229,6 +229,46 @@ def random_injection(seed: int, df: float, fdot: float = 0.0, rho: float = 20.0,
                      phi0=phi0, rho=rho, fddot=fddot)
 
 
+# injection record, one row per injected signal (mirrors ``fstat_injection``)
+INJECTION_DTYPE = np.dtype([
+    ("alpha", np.float64), ("delta", np.float64), ("psi", np.float64), ("cosi", np.float64),
+    ("phi0", np.float64), ("h0", np.float64), ("df", np.float64), ("fdot", np.float64),
+    ("fddot", np.float64), ("span_start", np.int64), ("span_len", np.int64),
+])
+
+
+def injection_records(injections, h0, span_start, span_len) -> np.ndarray:
+    """Pack Injection objects with amplitudes h0 and spans (broadcast) into
+    an INJECTION_DTYPE array."""
+    n = len(injections)
+    r = np.zeros(n, dtype=INJECTION_DTYPE)
+    for name in ("alpha", "delta", "psi", "cosi", "phi0", "df", "fdot", "fddot"):
+        r[name] = [getattr(i, name) for i in injections]
+    r["h0"] = np.broadcast_to(np.asarray(h0, np.float64), (n,))
+    r["span_start"] = np.broadcast_to(np.asarray(span_start, np.int64), (n,))
+    r["span_len"] = np.broadcast_to(np.asarray(span_len, np.int64), (n,))
+    return r
+
+
+def random_injection_records(n: int, seed: int, df: float, h0: float, span_len: int,
+                             span_start0: int = 0) -> np.ndarray:
+    """n injections on consecutive spans of span_len samples: isotropic sky,
+    uniform psi in [0, pi), cos(iota) in [-1, 1], phi0 in [0, 2 pi); common
+    df and h0, no spindown."""
+    g = rng(seed)
+    r = np.zeros(n, dtype=INJECTION_DTYPE)
+    r["alpha"] = g.uniform(0.0, 2.0 * math.pi, n)
+    r["delta"] = np.arcsin(g.uniform(-1.0, 1.0, n))
+    r["psi"] = g.uniform(0.0, math.pi, n)
+    r["cosi"] = g.uniform(-1.0, 1.0, n)
+    r["phi0"] = g.uniform(0.0, 2.0 * math.pi, n)
+    r["h0"] = h0
+    r["df"] = df
+    r["span_start"] = span_start0 + np.arange(n, dtype=np.int64) * span_len
+    r["span_len"] = span_len
+    return r
+
+
 def next_pow2(n: int) -> int:
     return 1 << max(0, int(n - 1).bit_length())
 

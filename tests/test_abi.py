@@ -7,6 +7,7 @@ import re
 import subprocess
 import tempfile
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -48,7 +49,7 @@ def _c_layout():
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', 'int main(void){']
     for cname, cls in (("fstat_detector", _lib.Detector), ("fstat_ephem", _lib.Ephem),
                        ("fstat_plan_desc", _lib.PlanDesc), ("fstat_template", _lib.Template),
-                       ("fstat_tuning", _lib.Tuning)):
+                       ("fstat_tuning", _lib.Tuning), ("fstat_injection", _lib.Injection)):
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
         for f, _ in cls._fields_:
             lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
@@ -69,7 +70,7 @@ def test_struct_layouts_match_header():
         got[(parts[0], parts[1])] = int(parts[2])
     for cname, cls in (("fstat_detector", _lib.Detector), ("fstat_ephem", _lib.Ephem),
                        ("fstat_plan_desc", _lib.PlanDesc), ("fstat_template", _lib.Template),
-                       ("fstat_tuning", _lib.Tuning)):
+                       ("fstat_tuning", _lib.Tuning), ("fstat_injection", _lib.Injection)):
         assert got[(cname, "size")] == ctypes.sizeof(cls)
         for f, _ in cls._fields_:
             assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
@@ -105,6 +106,21 @@ def test_null_arguments(lib):
     assert lib.fstat_status(None, None) == -1
     assert lib.fstat_compute(None, None, None, 0, None, 0, None, None) == -1
     lib.fstat_destroy(None)
+
+
+def test_inject_rejects_bad_arguments_on_the_host(lib):
+    """fstat_inject checks its plan, pointers and sizes before any launch."""
+    assert lib.fstat_inject(None, None, 0, 0, None, None) == -1               # no plan
+    assert lib.fstat_inject(None, None, 1, 86400, None, None) == -1
+
+
+def test_injection_records_match_the_struct():
+    import synth
+    from paper_0912_4255_gb300 import _lib
+    assert synth.INJECTION_DTYPE == _lib.INJECTION_DTYPE
+    r = synth.random_injection_records(3, 1, 0.01, 0.5, 1000, span_start0=7)
+    assert list(r["span_start"]) == [7, 1007, 2007] and np.all(r["span_len"] == 1000)
+    assert np.all(np.abs(r["delta"]) <= np.pi / 2) and np.all(np.abs(r["cosi"]) <= 1)
 
 
 def test_topk_rejects_bad_arguments_on_the_host(lib):
