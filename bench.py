@@ -194,15 +194,15 @@ def path_bytes(desc):
 def ncu_traffic(kernel: str, templates_per_launch: float):
     """DRAM bytes per launch from the committed ncu summary
     (profiles/traffic.md), scaled by templates per launch, or None if the
-    kernels changed since that capture (source digest mismatch)."""
+    path kernels changed since that capture (digest mismatch)."""
     path = os.path.join(ROOT, "profiles", "traffic.md")
     if not os.path.exists(path):
         return None
     try:
         from paper_0912_4255_gb300 import build as fsbuild
-        digest = fsbuild._sources_digest()
+        digest = fsbuild.path_digest()
         txt = open(path).read()
-        if f"digest: {digest}" not in txt:
+        if f"path digest: {digest}" not in txt:
             return None
         for line in txt.splitlines():
             p = [c.strip() for c in line.strip().strip("|").split("|")]

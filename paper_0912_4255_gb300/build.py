@@ -58,6 +58,28 @@ def _sources_digest() -> str:
     return h.hexdigest()
 
 
+# sources that compile or sequence the kernels of fstat_compute (time map,
+# resampler, A/B/C reduction, both FFT passes); other entry points (top-k,
+# injection, gradient, persistent and allocation-free modes) live elsewhere
+PATH_SOURCES = ("fstat_internal.cuh", "passes.cuh", "timemap.cu", "resample.cu", "cols.cu", "rows.cu",
+                "api.cu", "dispatch.cu")
+
+
+def path_digest() -> str:
+    """Digest of the fstat_compute kernels' sources and build flags: profile
+    summaries quote it so that a reader (and bench.py) can tell whether the
+    counters still describe the built kernels."""
+    h = hashlib.sha256()
+    inc = os.path.join(os.path.dirname(HERE), "include", "fstat.h")
+    for name in PATH_SOURCES + (inc,):
+        fp = os.path.join(CSRC, name)        # an absolute name stays as it is
+        with open(fp, "rb") as f:
+            h.update(os.path.basename(name).encode())
+            h.update(f.read())
+    h.update(" ".join(ARCH + FLAGS).encode())
+    return h.hexdigest()
+
+
 def build(jobs: int | None = None, verbose: bool = False, force: bool = False) -> str:
     """Compile every unit and link libfstat.so; returns the library path."""
     os.makedirs(OBJ, exist_ok=True)
