@@ -179,6 +179,19 @@ int fstat_get_tuning(fstat_plan_t p, fstat_tuning *t);
  * aligned).  The library zeroes its counters with cudaMemset. */
 int fstat_set_workspace(fstat_plan_t p, void *dev_ptr, size_t bytes);
 
+/* Output band (the interpolation remedy of Sec. V.B: resampling loses power
+ * toward the band edges, so a search covers twice the band it needs and
+ * keeps the lower half of the frequencies; with 2F stored in ascending
+ * frequency offset that half is bins n_fft/4 .. 3 n_fft/4).  fstat_compute
+ * then writes 2F only for bins q_lo <= q < q_hi, template t's values at
+ * out_off + (q - q_lo), and the default out_off becomes
+ * index * (q_hi - q_lo).  Default: the whole band [0, n_fft).  A partial
+ * band needs templates on the plan's n_fft (a template with its own n_fft
+ * gets FSTAT_ENOTSUP).  Errors: EINVAL (null plan), ERANGE (not
+ * 0 <= q_lo < q_hi <= n_fft). */
+int fstat_set_band(fstat_plan_t p, int64_t q_lo, int64_t q_hi);
+int fstat_get_band(fstat_plan_t p, int64_t *q_lo, int64_t *q_hi);
+
 /* Host helper: resampled length N_b of each template (host arrays), the
  * number of points of the uniform barycentric grid (Eq. 21).  A template
  * with an invalid span gets N_b = -1. */

@@ -134,6 +134,26 @@ class Plan:
                "fstat_set_tuning")
         self._attach(need.value)
 
+    def set_band(self, q_lo: int, q_hi: int):
+        """Write 2F only for bins q_lo <= q < q_hi (fstat_set_band)."""
+        _check(self.lib.fstat_set_band(self.handle, int(q_lo), int(q_hi)), "fstat_set_band")
+
+    def keep_lower_half(self):
+        """The band-doubling remedy of Sec. V.B: of a search over twice the
+        band it needs, keep the central half of the bins (|df| below a
+        quarter of the sampling rate)."""
+        n = int(self.desc.n_fft)
+        self.set_band(n // 4, 3 * n // 4)
+
+    def band(self) -> tuple:
+        lo, hi = ctypes.c_int64(), ctypes.c_int64()
+        _check(self.lib.fstat_get_band(self.handle, ctypes.byref(lo), ctypes.byref(hi)), "fstat_get_band")
+        return lo.value, hi.value
+
+    def band_len(self) -> int:
+        lo, hi = self.band()
+        return hi - lo
+
     def tuning(self) -> dict:
         t = _lib.Tuning()
         _check(self.lib.fstat_get_tuning(self.handle, ctypes.byref(t)), "fstat_get_tuning")
@@ -172,13 +192,14 @@ def _gap_args(gaps):
 
 
 def fstat_compute(plan: Plan, x_h, templates, gaps=None, twoF=None, stream=None):
-    """2F for every template and bin (float32, [n_templates * n_fft] unless
-    templates carry their own offsets)."""
+    """2F for every template and bin of the plan's output band (float32,
+    [n_templates * band length], the band being the whole n_fft unless
+    set_band narrowed it; templates may carry their own offsets)."""
     import torch
     assert x_h.is_cuda and x_h.dtype == torch.complex64 and x_h.is_contiguous()
     n_t = _n_templates(templates)
     if twoF is None:
-        twoF = torch.empty(n_t * int(plan.desc.n_fft), dtype=torch.float32, device=x_h.device)
+        twoF = torch.empty(n_t * plan.band_len(), dtype=torch.float32, device=x_h.device)
     g, ng = _gap_args(gaps)
     _check(plan.lib.fstat_compute(plan.handle, _ptr(x_h), _ptr(templates), n_t, g, ng,
                                   _ptr(twoF), _stream(stream)), "fstat_compute")
@@ -293,7 +314,7 @@ class GraphRunner:
         import torch
         self.plan, self.x_h, self.templates, self.gaps = plan, x_h, templates, gaps
         n_t = _n_templates(templates)
-        self.twoF = twoF if twoF is not None else torch.empty(n_t * int(plan.desc.n_fft),
+        self.twoF = twoF if twoF is not None else torch.empty(n_t * plan.band_len(),
                                                               dtype=torch.float32, device=x_h.device)
         self.stream = torch.cuda.Stream(device=x_h.device)
         if warmup:   # first calls set kernel attributes outside the capture

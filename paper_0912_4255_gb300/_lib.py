@@ -88,6 +88,8 @@ SYMBOLS = {
     "fstat_debug_stall": (ctypes.c_int, [c_void_p, c_int64]),
     "fstat_topk": (ctypes.c_int, [c_void_p, c_int64, c_int64, c_int64, ctypes.c_int, c_void_p, c_void_p,
                                   c_void_p]),
+    "fstat_set_band": (ctypes.c_int, [c_void_p, c_int64, c_int64]),
+    "fstat_get_band": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64)]),
     "fstat_inject": (ctypes.c_int, [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_void_p]),
     "fstat_profile": (ctypes.c_int, [c_void_p, ctypes.c_int]),
     "fstat_profile_read": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int64),

@@ -294,6 +294,8 @@ int fstat_plan(fstat_plan_t* out, const fstat_plan_desc* d, size_t* workspace_by
   pc.au = d->eph.au_m; pc.year = d->eph.year_s; pc.sid = d->eph.sidereal_day_s;
   pc.obliq = d->eph.obliquity_rad; pc.orb0 = d->eph.orb_phase0; pc.sid0 = d->eph.sid_phase0;
   derive_constants(pc);
+  pc.band_lo = 0;
+  pc.band_hi = d->n_fft;
   p->log2n = ilog2(d->n_fft);
   p->rec_bytes = d->precision == FSTAT_PREC_FP64 ? (int)sizeof(KnotD) : (int)sizeof(KnotF);
   p->cplx_bytes = d->precision == FSTAT_PREC_FP64 ? 16 : 8;
@@ -483,6 +485,21 @@ int fstat_profile_read(fstat_plan_t p, double* ms, int64_t* launches, int n_kind
   for (int k = 0; k < n_kinds; ++k) { ms[k] = acc[k]; launches[k] = p->launches[k]; }
   for (int k = 0; k < kKinds; ++k) p->launches[k] = 0;
   return rc;
+}
+
+int fstat_set_band(fstat_plan_t p, int64_t q_lo, int64_t q_hi) {
+  if (!p) return FSTAT_EINVAL;
+  if (q_lo < 0 || q_hi <= q_lo || q_hi > p->d.n_fft) return FSTAT_ERANGE;
+  p->pc.band_lo = q_lo;
+  p->pc.band_hi = q_hi;
+  return FSTAT_OK;
+}
+
+int fstat_get_band(fstat_plan_t p, int64_t* q_lo, int64_t* q_hi) {
+  if (!p || !q_lo || !q_hi) return FSTAT_EINVAL;
+  *q_lo = p->pc.band_lo;
+  *q_hi = p->pc.band_hi;
+  return FSTAT_OK;
 }
 
 int fstat_inject(fstat_plan_t p, const fstat_injection* inj, int64_t n_inj, int64_t max_span_len, float* x_h,

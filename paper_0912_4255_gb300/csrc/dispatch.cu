@@ -95,6 +95,7 @@ static cudaError_t do_rows(const PlanConst& pc, const Chunk& c, const Shape& sh,
   while ((1 << lc) < sh.cols) ++lc;
   a.log2cols = lc;
   a.blocks_max = (1 << sh.l1) / sh.rows;
+  a.band = !(pc.band_lo == 0 && pc.band_hi == ((int64_t)1 << sh.log2n));
   dim3 grid((unsigned)a.blocks_max, ti >= 0 ? 1u : (unsigned)c.nt);
   return rows_any<R>(a, sh.l2, grid, s);
 }

@@ -39,6 +39,9 @@ struct PlanConst {
   double wo, ws;                                  // orbital and sidereal rates (rad/s)
   double th0;                                     // sidereal angle of the meridian at t = 0
   double inv_dt;                                  // 1 / dt
+  // output band: 2F is written for bins band_lo <= q < band_hi only, at
+  // out_off + q - band_lo
+  int64_t band_lo, band_hi;
 };
 
 // Per-template state produced by the time-map kernel and completed by the

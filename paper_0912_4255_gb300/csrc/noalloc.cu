@@ -175,6 +175,8 @@ extern "C" int fstat_compute_noalloc(const fstat_plan_desc* d, const float* x_h,
   pc.log2h = fabs(d->f_het * d->dt) <= 100.0 ? 10 : kNaMinLog2h;
   pc.pad_ = 0;
   derive_constants(pc);
+  pc.band_lo = 0;
+  pc.band_hi = d->n_fft;
 
   int L = 0;
   while (((int64_t)1 << L) < d->n_fft) ++L;

@@ -51,6 +51,7 @@ struct RowsArgs {
   int cols;      // C of pass A
   int log2cols;
   int blocks_max; // row blocks of one template
+  int band;       // the plan's output band is partial (k_rows<..., true>)
 };
 
 // --------------------------------------------------------------- shapes
@@ -314,7 +315,9 @@ __device__ __forceinline__ void rows_tables(const Tw<R>& tw, cpx<R>* buf) {
 
 // One row block of pass B for template t (stage tables from rows_tables);
 // za: the template's intermediate.
-template <typename R, int L2, int RR, int NT>
+// BAND: the plan writes a partial output band (bins band_lo <= q < band_hi
+// only); without it every bin is stored, with no band test.
+template <typename R, int L2, int RR, int NT, bool BAND>
 __device__ __forceinline__ void rows_tile(const RowsArgs<R>& a, int t, int blk, cpx<R>* __restrict__ buf,
                                           const cpx<R>* __restrict__ zbase) {
   using Cx = cpx<R>;
@@ -325,10 +328,23 @@ __device__ __forceinline__ void rows_tile(const RowsArgs<R>& a, int t, int blk, 
   const int N1 = 1 << (L - L2);
   const int r0 = blk * RR;
   float* out = a.out + m.out_off;
+  // with BAND, bin q (ascending frequency) goes to out[q - band_lo] when
+  // band_lo <= q < band_hi (bins are below 2^24: 32-bit offsets)
+  int lo = 0, hi = 0;
+  if constexpr (BAND) {
+    lo = (int)a.pc.band_lo;
+    hi = (int)(a.pc.band_hi < ((int64_t)1 << L) ? a.pc.band_hi : ((int64_t)1 << L));
+    out -= lo;
+  }
   if (m.status != FSTAT_OK) {
     for (int i = threadIdx.x; i < RR * N2; i += NT) {
       const int r = i & (RR - 1), p2 = i / RR;
-      out[(int64_t)(r0 + r) + (int64_t)N1 * ((p2 + N2 / 2) & (N2 - 1))] = __int_as_float(0x7fc00000);
+      if constexpr (BAND) {
+        const int qb = (r0 + r) + N1 * ((p2 + N2 / 2) & (N2 - 1));
+        if (qb >= lo && qb < hi) out[qb] = __int_as_float(0x7fc00000);
+      } else {
+        out[(int64_t)(r0 + r) + (int64_t)N1 * ((p2 + N2 / 2) & (N2 - 1))] = __int_as_float(0x7fc00000);
+      }
     }
     return;
   }
@@ -401,13 +417,17 @@ __device__ __forceinline__ void rows_tile(const RowsArgs<R>& a, int t, int blk, 
     for (int q = 0; q < RADL; ++q) {
       const R v = ca * (fa[q].x * fa[q].x + fa[q].y * fa[q].y) + cb * (fb[q].x * fb[q].x + fb[q].y * fb[q].y)
                 + cc * (fa[q].x * fb[q].x + fa[q].y * fb[q].y);
+      if constexpr (BAND) {
+        const int qb = (r0 + r) + N1 * j + q * (N1 * NS) + (q < RADL / 2 ? 1 : -1) * (N1 * (N2 / 2));
+        if (qb < lo || qb >= hi) continue;
+      }
       __stcs(oq + q * s1 + (q < RADL / 2 ? hh : -hh), (float)v);
     }
   }
 }
 
 // Persistent over the (template, row block) items of a chunk.
-template <typename R, int L2, int RR, int NT>
+template <typename R, int L2, int RR, int NT, bool BAND>
 __global__ void __launch_bounds__(NT, (blocks_for_smem(rows_smem<R, L2, RR>()))) k_rows(RowsArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* buf = reinterpret_cast<cpx<R>*>(smem_raw);
@@ -440,7 +460,7 @@ __global__ void __launch_bounds__(NT, (blocks_for_smem(rows_smem<R, L2, RR>())))
     }
     if (blk * RR >= (1 << (m.log2n - L2))) continue;
     const cpx<R>* za = reinterpret_cast<const cpx<R>*>(a.c.za) + (int64_t)t * a.c.z_stride;
-    rows_tile<R, L2, RR, NT>(a, t, blk, buf, za);
+    rows_tile<R, L2, RR, NT, BAND>(a, t, blk, buf, za);
     __syncthreads();                      // the next block reuses buf
   }
 }

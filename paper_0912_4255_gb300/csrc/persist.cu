@@ -90,7 +90,7 @@ template <int L2>
 __device__ __noinline__ void rows_call(const RowsArgs<float>& a, int t, int blk, float2* buf, const float2* za) {
   rows_tables<float, L2, cols_for<float, kPP>(L2), kPT>(a.tw, buf);
   __syncthreads();
-  rows_tile<float, L2, cols_for<float, kPP>(L2), kPT>(a, t, blk, buf, za);
+  rows_tile<float, L2, cols_for<float, kPP>(L2), kPT, true>(a, t, blk, buf, za);
 }
 
 template <int SRC, int TAPS>
@@ -239,7 +239,7 @@ cudaError_t launch_persist(const PlanConst& pc, const Chunk& c, const float2* x,
   p.ca.pc = pc; p.ca.c = c; p.ca.x = x; p.ca.gaps = gaps; p.ca.wcs = wcs;
   p.ca.tw = *reinterpret_cast<const Tw<float>*>(twf);
   p.ca.ti = -1; p.ca.tiles_max = 0; p.ca.status = status; p.ca.rr = 1; p.ca.log2rr = 0;
-  p.ra.pc = pc; p.ra.c = c; p.ra.tw = p.ca.tw; p.ra.out = out; p.ra.ti = -1; p.ra.cols = 1; p.ra.log2cols = 0; p.ra.blocks_max = 0;
+  p.ra.pc = pc; p.ra.c = c; p.ra.tw = p.ca.tw; p.ra.out = out; p.ra.ti = -1; p.ra.cols = 1; p.ra.log2cols = 0; p.ra.blocks_max = 0; p.ra.band = 1;
   p.zslots = zslots;
   p.z_stride = z_stride;
   p.sched = sched;

@@ -20,12 +20,12 @@ cudaError_t FS_CAT(rows, FS_REAL, FS_L2)(const RowsArgs<FS_REAL>& a, dim3 grid, 
   constexpr int RR = cols_for<R>(L2);
   constexpr int NT = threads_for<R>(L2, 2 * RR);
   constexpr size_t SM = rows_smem<R, L2, RR>();
-  auto kern = k_rows<R, L2, RR, NT>;
-  static int attr_done = 0;
-  if (!attr_done) {
+  auto kern = a.band ? k_rows<R, L2, RR, NT, true> : k_rows<R, L2, RR, NT, false>;
+  static int attr_done[2] = {0, 0};
+  if (!attr_done[a.band ? 1 : 0]) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM);
     if (e != cudaSuccess) return e;
-    attr_done = 1;
+    attr_done[a.band ? 1 : 0] = 1;
   }
   // persistent grid: the blocks that fit on the device at once
   static int resident = 0;

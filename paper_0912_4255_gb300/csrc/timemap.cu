@@ -150,6 +150,9 @@ k_timemap(PlanConst pc, const fstat_template* __restrict__ tmpl, TmplMeta* __res
     else if (!allow_ragged && l != log2n_plan) st = st ? st : FSTAT_ENOTSUP;
     else log2n = l;
   }
+  // a partial output band is defined on the plan's n_fft only
+  if (log2n != log2n_plan && (pc.band_lo != 0 || pc.band_hi != ((int64_t)1 << log2n_plan)))
+    st = st ? st : FSTAT_ENOTSUP;
   // grid start and end: two threads evaluate t_b(t_s) and t_b(t_e)
   __shared__ double tb_sh[2];
   if (threadIdx.x < 2) {
@@ -184,7 +187,7 @@ k_timemap(PlanConst pc, const fstat_template* __restrict__ tmpl, TmplMeta* __res
       m.tb0 = tb0;
       m.A = m.B = m.C = 0.0;
       m.n_b = st == FSTAT_OK ? n_b : 0;
-      m.out_off = tp.out_off >= 0 ? tp.out_off : (tmpl_base + t) * ((int64_t)1 << log2n_plan);
+      m.out_off = tp.out_off >= 0 ? tp.out_off : (tmpl_base + t) * (pc.band_hi - pc.band_lo);
       m.span_lo = tp.span_start;
       m.span_hi = tp.span_start + tp.span_len;
       m.gap_off = tp.gap_off;

@@ -338,6 +338,28 @@ def test_nearest_neighbour_loss_is_sinc_squared():
     assert abs((1 - expect) - fct["order"]) < 0.1
 
 
+def test_doubling_the_band_follows_the_sinc_squared_law():
+    """Sec. V.B's remedy, nearest neighbour: the same signal in data
+    sampled twice as fast (dt / 2, twice the band) loses only
+    1 - sinc^2(df dt / 2) of its power, and the signal's bin then lies in
+    the central half of the doubled band, the half that is kept."""
+    ratios = []
+    for seed in (24, 25, 26):
+        plan = synth.PlanDesc(dt=0.25, n_data=5 * 86400 * 2, n_fft=1 << 20, interp=R.NEAREST,
+                              f_het=100.0)
+        k = round(0.7 * plan.n_fft * plan.dt)
+        df = k / (plan.n_fft * plan.dt)
+        assert plan.n_fft // 4 <= plan.n_fft // 2 + k < 3 * plan.n_fft // 4
+        inj = synth.random_injection(seed, df=df)
+        x, info = I.inject(np.zeros(plan.n_data), [inj], plan, I.valid_all(plan))
+        tm = synth.make_templates(inj.alpha, inj.delta, 0.0, 0, plan.n_data)[0]
+        r = F.resample_two_f(x, tm, NOGAPS, plan)
+        ratios.append(r[plan.n_fft // 2 + k] / info[0][1])
+    expect = np.sinc(df * plan.dt) ** 2               # 0.903 at 0.7 Hz, against 0.657 at dt = 0.5 s
+    assert abs(np.mean(ratios) - expect) < 0.03
+    assert np.mean(ratios) > np.sinc(df * 0.5) ** 2 + 0.2
+
+
 def test_chi2_four_dof_in_noise():
     """Sec. IV.B: in Gaussian noise 2F is chi^2 with 4 degrees of freedom
     (mean 4, variance 8), here through the whole resampling path."""
