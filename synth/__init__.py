@@ -269,6 +269,78 @@ def random_injection_records(n: int, seed: int, df: float, h0: float, span_len: 
     return r
 
 
+# --------------------------------------------------------------------------
+# SFT inputs (the data product of Eq. e25) for the front end
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class SftDesc:
+    """Front-end parameters (mirrors ``fstat_sft_desc``): raw samples per SFT
+    and raw sampling interval, the stored bins k_lo .. k_lo + n_bins - 1 of
+    every SFT, the heterodyne bin k_het (f_h = k_het / T_SFT), the bins per
+    SFT of the output band (output interval T_SFT / band_bins), Dirichlet
+    terms on each side, running-median window (0: no normalisation), Tukey
+    taper fraction of the band and time-domain taper at chunk ends."""
+    sft_len: int = 2048
+    dt_raw: float = 1.0 / 256.0
+    k_lo: int = 0
+    n_bins: int = 0
+    k_het: int = 0
+    band_bins: int = 64
+    dirichlet_terms: int = 16
+    median_window: int = 0
+    tukey_frac: float = 0.0
+    edge_taper: int = 0
+
+    def replace(self, **kw) -> "SftDesc":
+        return dataclasses.replace(self, **kw)
+
+    @property
+    def t_sft(self) -> float:
+        return self.sft_len * self.dt_raw
+
+
+def sft_slots(n_slots: int, missing: int, seed: int, max_run: int = 3) -> np.ndarray:
+    """Indices of the SFTs present among n_slots consecutive SFT slots, with
+    ``missing`` slots removed in runs of 1..max_run (never the first)."""
+    g = rng(seed)
+    keep = np.ones(n_slots, bool)
+    while (~keep).sum() < missing:
+        a = int(g.integers(1, n_slots))
+        keep[a:a + int(g.integers(1, max_run + 1))] = False
+    return np.nonzero(keep)[0]
+
+
+def raw_sinusoids(n: int, dt: float, freqs, amps, phases, t0: float = 0.0) -> np.ndarray:
+    """Real series sum_i A_i cos(2 pi f_i (t - t0) + phi_i) at t = t0 + j dt."""
+    t = np.arange(n) * dt
+    x = np.zeros(n)
+    for f, a, p in zip(freqs, amps, phases):
+        x += a * np.cos(2.0 * math.pi * f * t + p)
+    return x
+
+
+def sfts_of(x_raw: np.ndarray, slots, sft_len: int, k_lo: int, n_bins: int,
+            dtype=np.complex64) -> np.ndarray:
+    """SFT bins k_lo .. k_lo + n_bins - 1 of the SFTs at the given slots of a
+    raw real series (Eq. e25 by numpy's FFT), [len(slots), n_bins]."""
+    out = np.empty((len(slots), n_bins), dtype)
+    for i, a in enumerate(slots):
+        X = np.fft.fft(x_raw[a * sft_len:(a + 1) * sft_len])
+        out[i] = X[k_lo:k_lo + n_bins]
+    return out
+
+
+def sft_noise(n_sft: int, n_bins: int, sft_len: int, sigma2_raw: float, seed: int,
+              dtype=np.complex64) -> np.ndarray:
+    """SFT bins of white real noise of variance sigma2_raw drawn directly:
+    away from DC and Nyquist they are independent circular complex Gaussians
+    with E|X|^2 = sft_len * sigma2_raw."""
+    g = rng(seed)
+    s = math.sqrt(sft_len * sigma2_raw / 2.0)
+    return (g.normal(0.0, s, (n_sft, n_bins)) + 1j * g.normal(0.0, s, (n_sft, n_bins))).astype(dtype)
+
+
 def next_pow2(n: int) -> int:
     return 1 << max(0, int(n - 1).bit_length())
 
