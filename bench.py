@@ -264,10 +264,11 @@ def main():
                     help="log2 of the first-pass FFT length (0: the library's default)")
     ap.add_argument("--copy-streams", type=int, default=4,
                     help="streams the end-to-end leg splits each batch's device-to-host copy over")
-    ap.add_argument("--workload", default="search", choices=["search", "batch", "montecarlo"],
+    ap.add_argument("--workload", default="search", choices=["search", "batch", "montecarlo", "frontend"],
                     help="search: the 8192-template grid (the metric's workload); batch: 4096 "
                          "templates with uneven spans, own gap lists and FFT lengths; montecarlo: "
-                         "noise-only realizations of the 12 h nearest-neighbour configuration")
+                         "noise-only realizations of the 12 h nearest-neighbour configuration; frontend: "
+                         "the SFT front end making the search's 10 d series from 1800 s SFTs")
     ap.add_argument("--realizations", type=int, default=1 << 20,
                     help="Monte Carlo realizations (--workload montecarlo), noise only and with signals")
     ap.add_argument("--mc-h0", type=float, default=0.12,
@@ -289,6 +290,8 @@ def main():
         return run_batch(args)
     if args.workload == "montecarlo":
         return run_montecarlo(args)
+    if args.workload == "frontend":
+        return run_frontend(args)
 
     import torch
     import torch.distributed as dist
@@ -549,6 +552,78 @@ def run_e2e_candidates(fs, plan, desc, x_np, tm, gaps_np, dev, args, world, batc
             "ms_per_step": wall * 1e3, "steps": steps, "band_len": band_len, "k": k}
 
 
+def run_frontend(args):
+    """The SFT front end (Sec. III.B) at the search workload's size: 10 d of
+    1800 s SFTs of 256 Hz data (480 slots, 10 % missing in runs of 1-3),
+    3648 stored bins around f_h = 100 Hz, a 2 Hz output band (3600 bins per
+    SFT, dt_out = 0.5 s), 33 Dirichlet terms, a 101-bin running median and a
+    5 % Tukey taper; the output is the search's 1,728,000-sample series.
+    SFT noise bins are drawn directly (white noise: independent complex
+    Gaussian bins).  Device-timed with CUDA events over K passes, inputs
+    resident; e2e adds the host-to-device copy of the SFTs and the
+    device-to-host copy of the series."""
+    import torch
+    import paper_0912_4255_gb300 as fs
+    from paper_0912_4255_gb300 import build as fsbuild
+    fsbuild.build()
+    dev = torch.device("cuda", 0)
+    n_slots, t_len, fs_raw = 480, 1800.0, 256.0
+    n1, dk, pad, k_h = 3600, 16, 8, 180000
+    d = synth.SftDesc(sft_len=int(t_len * fs_raw), dt_raw=1.0 / fs_raw, k_lo=k_h - n1 // 2 - dk - pad,
+                      n_bins=n1 + 2 * (dk + pad), k_het=k_h, band_bins=n1, dirichlet_terms=dk,
+                      median_window=101, tukey_frac=0.05)
+    slots = synth.sft_slots(n_slots, n_slots // 10, synth.SEED_BASE + 80)
+    X_h = synth.sft_noise(len(slots), d.n_bins, d.sft_len, 1.0, synth.SEED_BASE + 81)
+    t_sft = slots * t_len
+    n_out = n_slots * n1
+    X = torch.from_numpy(X_h).to(dev)
+    x = torch.empty(n_out, dtype=torch.complex64, device=dev)
+    ws = torch.empty(fs.fstat_sft_workspace(d, len(slots)) + 256, dtype=torch.uint8, device=dev)
+    for _ in range(max(args.warmup, 1)):
+        fs.fstat_sft_series(d, X, t_sft, 0.0, n_out, x_h=x, workspace=ws)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        fs.fstat_sft_series(d, X, t_sft, 0.0, n_out, x_h=x, workspace=ws)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    # end to end: SFTs from pinned host memory, series back to pinned host memory
+    Xp = torch.from_numpy(X_h).pin_memory()
+    xp = torch.empty(n_out, dtype=torch.complex64).pin_memory()
+    torch.cuda.synchronize(dev)
+    e0.record()
+    for _ in range(args.steps):
+        X.copy_(Xp, non_blocking=True)
+        fs.fstat_sft_series(d, X, t_sft, 0.0, n_out, x_h=x, workspace=ws)
+        xp.copy_(x, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms_e2e = e0.elapsed_time(e1) / args.steps
+    n_chunks = len(synth_chunks(t_sft, t_len))
+    print(json.dumps({
+        "workload": "frontend",
+        "config": "10 d of 1800 s SFTs at 256 Hz (480 slots, 48 missing), 3648 stored bins, f_h = 100 Hz, "
+                  "2 Hz band (3600 bins per SFT), dk = 16, median window 101, Tukey 5 %",
+        "sfts": int(len(slots)), "chunks": n_chunks, "x_h_samples": n_out,
+        "ms": ms, "x_h_samples_per_s": n_out / (ms / 1e3),
+        "sft_bins_per_s": len(slots) * d.n_bins / (ms / 1e3),
+        "e2e": {"ms": ms_e2e, "h2d_bytes": int(X_h.nbytes), "d2h_bytes": int(n_out * 8)},
+        "gpu_launches_per_pass": 1 + 5 * n_chunks,          # normalisation + 5 per chunk
+        "steps": args.steps, "warmup": args.warmup}))
+
+
+def synth_chunks(t_sft, t_len):
+    """Contiguous runs of SFT start times (host bookkeeping for the report)."""
+    out, a = [], 0
+    for i in range(1, len(t_sft) + 1):
+        if i == len(t_sft) or abs(t_sft[i] - t_sft[i - 1] - t_len) > 1e-6:
+            out.append((a, i - a))
+            a = i
+    return out
+
+
 def run_montecarlo(args):
     """The paper's validation at its scale (Sec. IV.B: 2F is chi^2_4 in
     Gaussian noise, non-central chi^2_4 with a signal): R noise-only
@@ -578,6 +653,8 @@ def run_montecarlo(args):
     out = torch.empty(per * desc.n_fft, dtype=torch.float32, device=dev)
     thr = (10.0, 20.0, 30.0)
     acc = torch.zeros(5, dtype=torch.float64, device=dev)     # sum, sum of squares, tail counts
+    hist_edges = 40                                           # unit-width bins of 2F on [0, 40)
+    hist = torch.zeros(hist_edges, dtype=torch.float64, device=dev)
     scale = math.sqrt(desc.sigma2 / 2.0)
 
     def batch():
@@ -588,10 +665,12 @@ def run_montecarlo(args):
         acc[1] += out.square().sum(dtype=torch.float64)
         for i in range(3):
             acc[2 + i] += (out > thr[i]).sum()
+        hist.add_(torch.histc(out, bins=hist_edges, min=0.0, max=float(hist_edges)).double())
 
     batch()                                   # warm-up (not counted)
     torch.cuda.synchronize(dev)
     acc.zero_()
+    hist.zero_()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
     for _ in range(total // per):
@@ -606,8 +685,18 @@ def run_montecarlo(args):
     tails = {f"P(2F>{int(t)})": {"measured": float(acc[2 + i]) / n,
                                  "chi2_4": math.exp(-t / 2) * (1 + t / 2)}
              for i, t in enumerate((10.0, 20.0, 30.0))}
+    # histogram against chi^2_4: P(a <= 2F < a + 1) = G(a) - G(a + 1), G(x) = e^{-x/2}(1 + x/2)
+    sf = [math.exp(-a / 2) * (1 + a / 2) for a in range(hist_edges + 1)]
+    h = hist.cpu().numpy() / n
+    p_bin = np.array([sf[a] - sf[a + 1] for a in range(hist_edges)])
+    sig = np.sqrt(p_bin * (1 - p_bin) / n)
     noise_only = {"realizations": total, "two_f_values": n, "ms": ms, "two_f_values_per_s": n / (ms / 1e3),
-                  "mean": mean, "var": var, "chi2_4": {"mean": 4.0, "var": 8.0}, "tails": tails}
+                  "mean": mean, "var": var, "chi2_4": {"mean": 4.0, "var": 8.0}, "tails": tails,
+                  "histogram": {"bins": "unit width on [0, 40)",
+                                "max_rel_dev_bins_0_20": float(np.max(np.abs(h[:20] / p_bin[:20] - 1))),
+                                "max_dev_in_binomial_sigma": float(np.max(np.abs(h - p_bin) / sig)),
+                                "note": "neighbouring bins of a zero-padded FFT are correlated, so the "
+                                        "binomial sigma understates the scatter"}}
 
     # --- with signals: every realization carries one injection (isotropic
     # sky and orientation, h0 = args.mc_h0, frequency on bin q) added on the
@@ -627,6 +716,8 @@ def run_montecarlo(args):
     ib, tb = fs.INJECTION_DTYPE.itemsize * per, synth.TEMPLATE_DTYPE.itemsize * per
     sig = torch.empty(span * per, dtype=torch.complex64, device=dev)
     acc2 = torch.zeros(5, dtype=torch.float64, device=dev)   # sum z, sum z^2, sum (2F - 4), sum lambda, n(lambda > 0)
+    f_all = torch.empty(n_b * per, dtype=torch.float64, device=dev)     # 2F and lambda at bin q, for the
+    lam_all = torch.empty(n_b * per, dtype=torch.float64, device=dev)   # non-central histogram
 
     def sbatch(b):
         rb, tmb = inj_dev[b * ib:(b + 1) * ib], tm_dev[b * tb:(b + 1) * tb]
@@ -645,6 +736,8 @@ def run_montecarlo(args):
         acc2[2] += (f - 4.0).sum()
         acc2[3] += lam.sum()
         acc2[4] += (lam > 0).sum()
+        f_all[b * per:(b + 1) * per] = f
+        lam_all[b * per:(b + 1) * per] = lam
 
     sbatch(0)                                 # warm-up (not counted)
     torch.cuda.synchronize(dev)
@@ -657,10 +750,22 @@ def run_montecarlo(args):
     rc = rc or fs.fstat_status(plan, raise_error=False)
     ms2 = ev0.elapsed_time(ev1)
     zm = float(acc2[0]) / total
+    # probability integral transform u = CDF_{ncx2(4, lambda)}(2F): uniform on
+    # [0, 1) when 2F is non-central chi^2_4 with the noise-free 2F as lambda
+    try:
+        from scipy.stats import ncx2
+        u = ncx2.cdf(f_all.cpu().numpy(), 4, lam_all.cpu().numpy())
+        hu, _ = np.histogram(u, bins=20, range=(0.0, 1.0))
+        pit = {"bins": 20, "max_rel_dev": float(np.max(np.abs(hu / (total / 20) - 1))),
+               "binomial_rel_sigma": float(math.sqrt(19 / total)),
+               "ks_stat": float(np.max(np.abs(np.sort(u) - (np.arange(total) + 0.5) / total)))}
+    except ImportError:
+        pit = None
     with_signal = {"realizations": total, "h0": args.mc_h0, "bin": q_off, "ms": ms2,
                    "mean_lambda": float(acc2[3]) / total,
                    "z_mean": zm, "z_var": float(acc2[1]) / total - zm * zm,
                    "sum_2F_minus_4_over_sum_lambda": float(acc2[2]) / float(acc2[3]),
+                   "pit_histogram": pit,
                    "expected": {"z_mean": 0.0, "z_var": 1.0, "ratio": 1.0}}
     print(json.dumps({
         "workload": "montecarlo",

@@ -147,6 +147,25 @@ typedef struct fstat_injection {
   int64_t span_start, span_len;
 } fstat_injection;
 
+/* SFT front end (Sec. III.B): how the heterodyned series is made from
+ * short Fourier transforms.  Every SFT holds the stored bins
+ * k_lo .. k_lo + n_bins - 1 of the DFT of sft_len raw samples at interval
+ * dt_raw (Eq. e25, T_SFT = sft_len dt_raw); k_het is the heterodyne bin
+ * (f_h = k_het / T_SFT); band_bins (even) is the output band in SFT bins,
+ * giving output samples every T_SFT / band_bins; dirichlet_terms is dk of
+ * Eq. e9; median_window (odd, 0 = none) the running-median window of the
+ * noise normalisation (Eq. dimlessSFTs1); tukey_frac the taper fraction of
+ * the output band (Sec. III.B.5); edge_taper the raised-cosine taper in
+ * samples at both ends of every chunk (Sec. III.B.6, 0 = none). */
+typedef struct fstat_sft_desc {
+  int64_t sft_len;
+  double dt_raw;
+  int64_t k_lo, n_bins, k_het, band_bins;
+  int32_t dirichlet_terms, median_window;
+  double tukey_frac;
+  int64_t edge_taper;
+} fstat_sft_desc;
+
 /* Kernel shape choices (set by the autotuner; zeros mean automatic).
  * log2_n1: log2 of the first-pass (column) FFT length; cols: columns per
  * block in the first pass; rows: rows per block in the second pass; chunk:
@@ -303,6 +322,38 @@ int fstat_topk(const float *twoF, int64_t n_rows, int64_t row_len, int64_t band_
  * samples), ECUDA.  Asynchronous on stream. */
 int fstat_inject(fstat_plan_t p, const fstat_injection *injections, int64_t n_inj,
                  int64_t max_span_len, float *x_h, void *stream);
+
+/* Device workspace of fstat_sft_series for n_sft SFTs (bytes; 0 if the
+ * descriptor is invalid). */
+size_t fstat_sft_workspace(const fstat_sft_desc *d, int64_t n_sft);
+
+/* Steps 2-6 of the front end (the summary of Sec. III.B.7) on the GPU:
+ * normalise every SFT by a running median of |X|^2 / ln 2; split the SFTs
+ * into chunks of consecutive SFTs (start times exactly T_SFT apart);
+ * merge each chunk of M SFTs into the band of the long transform with the
+ * truncated Dirichlet kernel (Eq. e9, P_{b,k} = sin y / y - i (1 - cos y) / y,
+ * y = 2 pi (b / M - k), 2 dk + 1 terms around k* = floor(b / M)); weight the
+ * N_out = band_bins M bins b = k_het M + m, -N_out/2 <= m < N_out/2, with
+ * the Tukey window and inverse transform them,
+ *   z[n] = 1 / sqrt(M N_out) sum_m w_m X_{k_het M + m} e^{2 pi i m n / N_out};
+ * multiply by e^{-2 pi i f_h (t_c - t_start)} (Eq. hetStartCorr with the sign
+ * of the heterodyne x_h = x e^{-2 pi i f_h (t - t_start)}), taper the chunk
+ * ends if asked and write it at sample (t_c - t_start) / dt_out of x_h;
+ * samples covered by no chunk are zero.
+ * sfts: device complex64 [n_sft][n_bins] (8-byte aligned); t_sft: host
+ * float64 [n_sft] start times, ascending; x_h: device complex64 [n_out];
+ * workspace: device, 256-byte aligned, fstat_sft_workspace bytes.
+ * Errors: EINVAL (null or misaligned pointer, bad descriptor: sft_len < 2,
+ * dt_raw <= 0, band_bins odd or < 2 or > 8192, dk < 0, median window even
+ * or > 1023, n_bins > 32768, tukey_frac outside [0, 1], edge_taper < 0,
+ * times not ascending), ERANGE (stored bins do not cover
+ * k_het - band_bins/2 - dk .. k_het + band_bins/2 - 1 + dk, a chunk start
+ * not on the output grid or outside x_h, a chunk of more than 65535 SFTs),
+ * ENOMEM (workspace too small),
+ * ECUDA.  Asynchronous on stream (the host part reads t_sft only). */
+int fstat_sft_series(const fstat_sft_desc *d, const float *sfts, const double *t_sft, int64_t n_sft,
+                     double t_start, int64_t n_out, float *x_h, void *workspace, size_t ws_bytes,
+                     void *stream);
 
 /* Synchronise the stream, return and clear the first device-side error
  * recorded since the last call (FSTAT_OK if none). */

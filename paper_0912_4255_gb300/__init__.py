@@ -25,7 +25,7 @@ __all__ = [
     "fstat_grad",
     "fstat_status", "fstat_destroy", "fstat_strerror", "fstat_template_nb", "pack_templates",
     "fstat_profile", "fstat_profile_read", "KERNEL_KINDS", "GraphRunner", "fstat_debug_stall", "fstat_topk",
-    "fstat_inject", "pack_injections", "INJECTION_DTYPE",
+    "fstat_inject", "pack_injections", "INJECTION_DTYPE", "fstat_sft_series", "fstat_sft_workspace",
     "NEAREST", "SINC", "WIN_RECT", "WIN_LANCZOS", "PREC_MIXED", "PREC_FP64", "PREC_FP32",
     "MODE_FUSED", "MODE_PLAIN", "MODE_PERSISTENT", "MODE_SPLIT", "TEMPLATE_DTYPE",
 ]
@@ -265,6 +265,42 @@ def fstat_inject(plan: Plan, x_h, injections, max_span_len: int | None = None, s
     n = injections.numel() // INJECTION_DTYPE.itemsize
     _check(plan.lib.fstat_inject(plan.handle, _ptr(injections), n, int(max_span_len), _ptr(x_h),
                                  _stream(stream)), "fstat_inject")
+    return x_h
+
+
+def _sft_desc(d) -> _lib.SftDesc:
+    """fstat_sft_desc from any object carrying the same field names."""
+    return _lib.SftDesc(int(d.sft_len), float(d.dt_raw), int(d.k_lo), int(d.n_bins), int(d.k_het),
+                        int(d.band_bins), int(d.dirichlet_terms), int(d.median_window), float(d.tukey_frac),
+                        int(d.edge_taper))
+
+
+def fstat_sft_workspace(desc, n_sft: int) -> int:
+    return int(_lib.load().fstat_sft_workspace(ctypes.byref(_sft_desc(desc)), int(n_sft)))
+
+
+def fstat_sft_series(desc, sfts, t_sft, t_start: float, n_out: int, x_h=None, workspace=None, stream=None):
+    """The heterodyned series from SFTs (steps 2-6 of Sec. III.B.7 on the
+    GPU).  sfts: device complex64 [n_sft, n_bins]; t_sft: host start times
+    (sequence of floats); returns x_h, device complex64 [n_out]."""
+    import torch
+    lib = _lib.load()
+    assert sfts.is_cuda and sfts.dtype == torch.complex64 and sfts.is_contiguous()
+    d = _sft_desc(desc)
+    t = np.ascontiguousarray(np.asarray(t_sft, np.float64))
+    n_sft = len(t)
+    if x_h is None:
+        x_h = torch.empty(int(n_out), dtype=torch.complex64, device=sfts.device)
+    need = int(lib.fstat_sft_workspace(ctypes.byref(d), n_sft))
+    if need == 0:
+        raise FstatError(-1, "fstat_sft_workspace")
+    if workspace is None or workspace.numel() < need + 256:
+        workspace = torch.empty(need + 256, dtype=torch.uint8, device=sfts.device)
+    off = (-workspace.data_ptr()) % 256
+    _check(lib.fstat_sft_series(ctypes.byref(d), _ptr(sfts), t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                n_sft, float(t_start), int(n_out), _ptr(x_h),
+                                ctypes.c_void_p(workspace.data_ptr() + off), workspace.numel() - off,
+                                _stream(stream)), "fstat_sft_series")
     return x_h
 
 

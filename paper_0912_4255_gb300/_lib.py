@@ -55,6 +55,12 @@ class Injection(ctypes.Structure):
                 ("fddot", c_double), ("span_start", c_int64), ("span_len", c_int64)]
 
 
+class SftDesc(ctypes.Structure):
+    _fields_ = [("sft_len", c_int64), ("dt_raw", c_double), ("k_lo", c_int64), ("n_bins", c_int64),
+                ("k_het", c_int64), ("band_bins", c_int64), ("dirichlet_terms", ctypes.c_int32),
+                ("median_window", ctypes.c_int32), ("tukey_frac", c_double), ("edge_taper", c_int64)]
+
+
 class Tuning(ctypes.Structure):
     _fields_ = [("mode", c_int32), ("log2_n1", c_int32), ("cols", c_int32),
                 ("rows", c_int32), ("chunk", c_int32), ("knot_log2", c_int32)]
@@ -90,6 +96,9 @@ SYMBOLS = {
                                   c_void_p]),
     "fstat_set_band": (ctypes.c_int, [c_void_p, c_int64, c_int64]),
     "fstat_get_band": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64)]),
+    "fstat_sft_workspace": (ctypes.c_size_t, [ctypes.POINTER(SftDesc), c_int64]),
+    "fstat_sft_series": (ctypes.c_int, [ctypes.POINTER(SftDesc), c_void_p, ctypes.POINTER(c_double), c_int64,
+                                        c_double, c_int64, c_void_p, c_void_p, ctypes.c_size_t, c_void_p]),
     "fstat_inject": (ctypes.c_int, [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_void_p]),
     "fstat_profile": (ctypes.c_int, [c_void_p, ctypes.c_int]),
     "fstat_profile_read": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int64),

@@ -1,0 +1,385 @@
+// SFT front end (Sec. III.B): SFTs -> normalised -> merged into the band of
+// the long transform (Eq. e9) -> windowed -> inverse transformed -> stitched
+// into the heterodyned series.
+//
+// Eq. e9 is evaluated in an exactly equivalent order.  With b = k* M + r
+// (0 <= r < M), e^{-2 pi i b alpha / M} = e^{-2 pi i r alpha / M} and
+// P_{b,k} depends on r and j = k - k* only, so
+//   X_b = sum_j P(r, j) D_{k*+j}(r),   D_k(r) = sum_alpha X^_{alpha,k} e^{-2 pi i r alpha / M},
+// a length-M DFT over the SFT index of every stored bin (k_dft_alpha) and a
+// (2 dk + 1)-term sum per output bin (k_merge).  The inverse transform of
+// length N_out = N1 M splits the same way (m = kappa M + r, n = n1 + N1 n2):
+//   z[n1 + N1 n2] = sum_r e^{2 pi i r n2 / M} e^{2 pi i r n1 / N_out}
+//                   sum_kappa Y[r][kappa] e^{2 pi i kappa n1 / N1},
+// two direct DFTs (k_idft_n1 over kappa, k_idft_n2 over r) with twiddle
+// indices taken exactly in integers.  The lengths (N1 = band bins per SFT,
+// M = SFTs per chunk) are arbitrary, not powers of two.
+#include "fstat_internal.cuh"
+
+#include <math.h>
+
+#include <vector>
+
+namespace fs {
+
+namespace {
+
+constexpr int kFeThreads = 256;
+constexpr int kMaxBins = 32768;      // stored bins per SFT (running median in shared memory)
+constexpr int kMaxN1 = 8192;         // band bins per SFT (inverse pass over kappa in shared memory)
+constexpr int kMaxWindow = 1023;
+
+// Step 2: X^ = X / sqrt(S), S = (lower) median of |X|^2 over the window / ln 2.
+__global__ void __launch_bounds__(kFeThreads)
+k_normalize(const float2* __restrict__ X, float2* __restrict__ Xh, int K, int w) {
+  extern __shared__ float P[];
+  const float2* x = X + (int64_t)blockIdx.x * K;
+  float2* y = Xh + (int64_t)blockIdx.x * K;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const float2 v = x[k];
+    P[k] = v.x * v.x + v.y * v.y;
+  }
+  __syncthreads();
+  const int h = w / 2;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const int lo = max(0, k - h), hi = min(K, k + h + 1);
+    const int t = (hi - lo - 1) / 2;           // rank of the (lower) median
+    float med = P[k];
+    for (int i = lo; i < hi; ++i) {
+      const float v = P[i];
+      int lt = 0, le = 0;
+      for (int j = lo; j < hi; ++j) {
+        const float u = P[j];
+        lt += u < v;
+        le += u <= v;
+      }
+      if (lt <= t && t < le) { med = v; break; }
+    }
+    const float s = rsqrtf(med * 1.4426950408889634f);   // 1 / sqrt(median / ln 2)
+    const float2 v = x[k];
+    y[k] = make_float2(v.x * s, v.y * s);
+  }
+}
+
+// Twiddle tables of one chunk: tm[j] = (cos, sin, 1 - cos) of 2 pi j / M,
+// tn[j] = (cos, sin) of 2 pi j / N1, from FP64.
+__global__ void k_tables(float4* __restrict__ tm, int M, float2* __restrict__ tn, int N1) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < M) {
+    double s, c, sh, ch;
+    sincospi(2.0 * i / M, &s, &c);
+    sincospi((double)i / M, &sh, &ch);
+    tm[i] = make_float4((float)c, (float)s, (float)(2.0 * sh * sh), 0.f);
+  }
+  if (i < N1) {
+    double s, c;
+    sincospi(2.0 * i / N1, &s, &c);
+    tn[i] = make_float2((float)c, (float)s);
+  }
+}
+
+// Step 4a: D[r][k] = sum_alpha Xh[alpha][k] e^{-2 pi i r alpha / M}.  Lanes
+// run over k (coalesced rows of Xh); every warp owns 8 consecutive r, whose
+// twiddles are the same for all its lanes.  grid (ceil(K / 32), ceil(M / 64)).
+constexpr int kRPerWarp = 8;
+__global__ void __launch_bounds__(kFeThreads)
+k_dft_alpha(const float2* __restrict__ Xh, int K, int M, const float4* __restrict__ tm, float2* __restrict__ D) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int k = blockIdx.x * 32 + lane;
+  const int r0 = (blockIdx.y * (kFeThreads / 32) + warp) * kRPerWarp;
+  if (r0 >= M) return;
+  float2 acc[kRPerWarp];
+  int idx[kRPerWarp], step[kRPerWarp];
+#pragma unroll
+  for (int q = 0; q < kRPerWarp; ++q) {
+    acc[q] = make_float2(0.f, 0.f);
+    idx[q] = 0;
+    step[q] = r0 + q < M ? r0 + q : 0;         // r beyond M: not written; keep its index in range
+  }
+  const bool live = k < K;
+  for (int a = 0; a < M; ++a) {
+    const float2 v = live ? __ldg(Xh + (int64_t)a * K + k) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < kRPerWarp; ++q) {
+      const float4 t = __ldg(tm + idx[q]);       // e^{-i theta} = (cos, -sin)
+      acc[q].x += v.x * t.x + v.y * t.y;
+      acc[q].y += v.y * t.x - v.x * t.y;
+      idx[q] += step[q];                         // (r alpha) mod M
+      if (idx[q] >= M) idx[q] -= M;
+    }
+  }
+  if (!live) return;
+#pragma unroll
+  for (int q = 0; q < kRPerWarp; ++q)
+    if (r0 + q < M) D[(int64_t)(r0 + q) * K + k] = acc[q];
+}
+
+// Step 4b + the Tukey window of step 5: for m = kappa M + r,
+// Y[r][kappa + N1/2] = w_m sum_{j=-dk}^{dk} P(r, j) D[r][k_s + j],
+// k_s = k_het - k_lo + kappa.  grid (ceil(N1 / 256), M).
+__global__ void __launch_bounds__(kFeThreads)
+k_merge(const float2* __restrict__ D, int K, int M, int N1, int ks0, int dk, const float4* __restrict__ tm,
+        double tukey_e, float2* __restrict__ Y) {
+  const int r = blockIdx.y;
+  const int kp = blockIdx.x * blockDim.x + threadIdx.x;      // kappa + N1/2
+  if (kp >= N1) return;
+  const int kappa = kp - N1 / 2;
+  const int ks = ks0 + kappa;
+  const float2* d = D + (int64_t)r * K;
+  float2 acc;
+  if (r == 0) {
+    acc = __ldg(d + ks);                      // y = 0 only at j = 0; P = 0 at the other SFT bins
+  } else {
+    const float4 t = __ldg(tm + r);
+    const float sn = t.y, omc = t.z;          // sin theta, 1 - cos theta
+    const float th = 6.283185307179586f * ((float)r / (float)M);
+    acc = make_float2(0.f, 0.f);
+    for (int j = -dk; j <= dk; ++j) {
+      const float iy = 1.0f / (th - 6.283185307179586f * (float)j);
+      const float pr = sn * iy, pi = -omc * iy;   // P = (sin theta - i (1 - cos theta)) / y
+      const float2 v = __ldg(d + ks + j);
+      acc.x += v.x * pr - v.y * pi;
+      acc.y += v.x * pi + v.y * pr;
+    }
+  }
+  // Tukey window over x = (i + 1/2) / N_out, i = m + N_out / 2
+  const int64_t n_out = (int64_t)N1 * M;
+  const int64_t i = (int64_t)kappa * M + r + n_out / 2;
+  const double x = ((double)i + 0.5) / (double)n_out;
+  float w = 1.f;
+  if (tukey_e > 0.0) {
+    if (x < tukey_e) w = (float)(0.5 * (1.0 - cospi(x / tukey_e)));
+    else if (x > 1.0 - tukey_e) w = (float)(0.5 * (1.0 - cospi((1.0 - x) / tukey_e)));
+  }
+  Y[(int64_t)r * N1 + kp] = make_float2(acc.x * w, acc.y * w);
+}
+
+// Step 5, first pass: U[r][n1] = e^{2 pi i r n1 / N_out} (-1)^{n1}
+// sum_{kp} Y[r][kp] e^{2 pi i kp n1 / N1}  (kp = kappa + N1/2).  One block per
+// r; the row of Y and the N1-table in shared memory; 4 outputs per thread.
+constexpr int kOutPerThread = 4;
+__global__ void __launch_bounds__(kFeThreads)
+k_idft_n1(const float2* __restrict__ Y, int N1, int M, const float2* __restrict__ tn, float2* __restrict__ U) {
+  extern __shared__ float2 sm[];
+  float2* ys = sm;
+  float2* ts = sm + N1;
+  const int r = blockIdx.y;
+  for (int i = threadIdx.x; i < N1; i += blockDim.x) {
+    ys[i] = __ldg(Y + (int64_t)r * N1 + i);
+    ts[i] = __ldg(tn + i);
+  }
+  __syncthreads();
+  const int base = blockIdx.x * (kFeThreads * kOutPerThread) + threadIdx.x;
+  float2 acc[kOutPerThread];
+  int idx[kOutPerThread], n1v[kOutPerThread];
+#pragma unroll
+  for (int q = 0; q < kOutPerThread; ++q) {
+    acc[q] = make_float2(0.f, 0.f);
+    idx[q] = 0;
+    n1v[q] = min(base + q * kFeThreads, N1 - 1);
+  }
+  for (int kp = 0; kp < N1; ++kp) {
+    const float2 y = ys[kp];
+#pragma unroll
+    for (int q = 0; q < kOutPerThread; ++q) {
+      const float2 t = ts[idx[q]];
+      acc[q].x += y.x * t.x - y.y * t.y;
+      acc[q].y += y.x * t.y + y.y * t.x;
+      idx[q] += n1v[q];                       // (kp n1) mod N1
+      if (idx[q] >= N1) idx[q] -= N1;
+    }
+  }
+  const int64_t n_out = (int64_t)N1 * M;
+#pragma unroll
+  for (int q = 0; q < kOutPerThread; ++q) {
+    const int n1 = base + q * kFeThreads;
+    if (n1 >= N1) continue;
+    double s, c;
+    sincospi(2.0 * (double)(((int64_t)r * n1) % n_out) / (double)n_out, &s, &c);
+    const float sg = (n1 & 1) ? -1.f : 1.f;  // e^{-pi i n1} from kappa = kp - N1/2
+    const float cs = (float)c * sg, sn = (float)s * sg;
+    U[(int64_t)r * N1 + n1] = make_float2(acc[q].x * cs - acc[q].y * sn, acc[q].x * sn + acc[q].y * cs);
+  }
+}
+
+// Step 5, second pass, and step 6: x_h[off + n1 + N1 n2] =
+// g taper(n) / sqrt(M N_out) sum_r U[r][n1] e^{2 pi i r n2 / M}.  Lanes run
+// over 32 consecutive n1 (coalesced U rows and output), every warp over
+// its own n2 values (warp-uniform twiddles); U staged in shared memory in
+// tiles of 64 r.  grid (ceil(N1 / 32), ceil(M / 64)).
+constexpr int kRTile = 64;
+constexpr int kN2PerBlock = 64;
+__global__ void __launch_bounds__(kFeThreads)
+k_idft_n2(const float2* __restrict__ U, int N1, int M, const float4* __restrict__ tm, float scale, float gc,
+          float gs, int64_t taper, int64_t off, float2* __restrict__ x) {
+  __shared__ float2 us[kRTile][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int n1 = blockIdx.x * 32 + lane;
+  constexpr int PER_WARP = kN2PerBlock / (kFeThreads / 32);
+  const int n2_0 = blockIdx.y * kN2PerBlock + warp * PER_WARP;
+  float2 acc[PER_WARP];
+  int idx[PER_WARP], step[PER_WARP];
+#pragma unroll
+  for (int q = 0; q < PER_WARP; ++q) {
+    acc[q] = make_float2(0.f, 0.f);
+    idx[q] = 0;
+    step[q] = n2_0 + q < M ? n2_0 + q : 0;     // n2 beyond M: not written; keep its index in range
+  }
+  for (int rt = 0; rt < M; rt += kRTile) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kRTile * 32; i += kFeThreads) {
+      const int rr = i / 32, l = i % 32;
+      const int gn1 = blockIdx.x * 32 + l;
+      us[rr][l] = (rt + rr < M && gn1 < N1) ? __ldg(U + (int64_t)(rt + rr) * N1 + gn1) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int rn = min(kRTile, M - rt);
+    for (int rr = 0; rr < rn; ++rr) {
+      const float2 u = us[rr][lane];
+#pragma unroll
+      for (int q = 0; q < PER_WARP; ++q) {
+        const float4 t = __ldg(tm + idx[q]);     // e^{+i theta}
+        acc[q].x += u.x * t.x - u.y * t.y;
+        acc[q].y += u.x * t.y + u.y * t.x;
+        idx[q] += step[q];                       // (r n2) mod M
+        if (idx[q] >= M) idx[q] -= M;
+      }
+    }
+  }
+  if (n1 >= N1) return;
+  const int64_t n_out = (int64_t)N1 * M;
+  const int64_t e = taper < n_out / 2 ? taper : n_out / 2;
+#pragma unroll
+  for (int q = 0; q < PER_WARP; ++q) {
+    const int n2 = n2_0 + q;
+    if (n2 >= M) continue;
+    const int64_t n = n1 + (int64_t)N1 * n2;
+    float g = scale;
+    if (e > 0) {
+      if (n < e) g *= (float)(0.5 * (1.0 - cospi(((double)n + 0.5) / (double)e)));
+      else if (n >= n_out - e) g *= (float)(0.5 * (1.0 - cospi(((double)(n_out - 1 - n) + 0.5) / (double)e)));
+    }
+    const float re = acc[q].x * gc - acc[q].y * gs, im = acc[q].x * gs + acc[q].y * gc;
+    x[off + n] = make_float2(re * g, im * g);
+  }
+}
+
+size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct FeLayout {
+  size_t xh, d, y, u, tm, tn, total;
+};
+
+FeLayout layout(const fstat_sft_desc& d, int64_t n_sft) {
+  FeLayout l;
+  const size_t K = (size_t)d.n_bins, N1 = (size_t)d.band_bins, M = (size_t)n_sft;
+  l.xh = 0;
+  l.d = l.xh + a256(M * K * 8);
+  l.y = l.d + a256(K * M * 8);
+  l.u = l.y + a256(N1 * M * 8);
+  l.tm = l.u + a256(N1 * M * 8);
+  l.tn = l.tm + a256(M * 16);
+  l.total = l.tn + a256(N1 * 8);
+  return l;
+}
+
+int check(const fstat_sft_desc* d) {
+  if (!d) return FSTAT_EINVAL;
+  if (d->sft_len < 2 || !(d->dt_raw > 0.0) || d->n_bins < 1 || d->n_bins > kMaxBins || d->band_bins < 2 ||
+      (d->band_bins & 1) || d->band_bins > kMaxN1 || d->dirichlet_terms < 0 || d->median_window < 0 ||
+      (d->median_window > 0 && !(d->median_window & 1)) || d->median_window > kMaxWindow ||
+      !(d->tukey_frac >= 0.0 && d->tukey_frac <= 1.0) || d->edge_taper < 0)
+    return FSTAT_EINVAL;
+  const int64_t need_lo = d->k_het - d->band_bins / 2 - d->dirichlet_terms;
+  const int64_t need_hi = d->k_het + d->band_bins / 2 - 1 + d->dirichlet_terms;
+  if (need_lo < d->k_lo || need_hi > d->k_lo + d->n_bins - 1) return FSTAT_ERANGE;
+  return FSTAT_OK;
+}
+
+}  // namespace
+
+}  // namespace fs
+
+extern "C" size_t fstat_sft_workspace(const fstat_sft_desc* d, int64_t n_sft) {
+  if (fs::check(d) != FSTAT_OK || n_sft < 0) return 0;
+  return fs::layout(*d, n_sft > 0 ? n_sft : 1).total;
+}
+
+extern "C" int fstat_sft_series(const fstat_sft_desc* d, const float* sfts, const double* t_sft, int64_t n_sft,
+                                double t_start, int64_t n_out, float* x_h, void* workspace, size_t ws_bytes,
+                                void* stream) {
+  using namespace fs;
+  int rc = check(d);
+  if (rc) return rc;
+  if (n_sft < 0 || n_out < 0 || !x_h || ((uintptr_t)x_h & 7)) return FSTAT_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (n_out > 0 && cudaMemsetAsync(x_h, 0, (size_t)n_out * 8, s) != cudaSuccess) return FSTAT_ECUDA;
+  if (n_sft == 0) return FSTAT_OK;
+  if (!sfts || !t_sft || !workspace || ((uintptr_t)sfts & 7) || ((uintptr_t)workspace & 255)) return FSTAT_EINVAL;
+  const FeLayout l = layout(*d, n_sft);
+  if (ws_bytes < l.total) return FSTAT_ENOMEM;
+  const double t_len = (double)d->sft_len * d->dt_raw;
+  const double dt_out = t_len / (double)d->band_bins;
+  const double f_h = (double)d->k_het / t_len;
+  // chunks of consecutive SFTs, their output offsets
+  struct Chunk1 { int64_t a, m, off; double tc; };
+  std::vector<Chunk1> ch;
+  int64_t a = 0;
+  for (int64_t i = 1; i <= n_sft; ++i) {
+    if (i < n_sft && !(t_sft[i] > t_sft[i - 1])) return FSTAT_EINVAL;
+    if (i == n_sft || fabs(t_sft[i] - t_sft[i - 1] - t_len) > 1e-6 * t_len) {
+      const double u = (t_sft[a] - t_start) / dt_out;
+      const double ur = nearbyint(u);
+      if (fabs(u - ur) > 1e-6 || ur < 0 || (int64_t)ur + (i - a) * d->band_bins > n_out) return FSTAT_ERANGE;
+      if (i - a > 65535 || i - a > 0x7fffffff / d->band_bins) return FSTAT_ERANGE;   // grid y, int indices
+      ch.push_back({a, i - a, (int64_t)ur, t_sft[a]});
+      a = i;
+    }
+  }
+  char* ws = static_cast<char*>(workspace);
+  float2* xh = reinterpret_cast<float2*>(ws + l.xh);
+  float2* D = reinterpret_cast<float2*>(ws + l.d);
+  float2* Y = reinterpret_cast<float2*>(ws + l.y);
+  float2* U = reinterpret_cast<float2*>(ws + l.u);
+  float4* tm = reinterpret_cast<float4*>(ws + l.tm);
+  float2* tn = reinterpret_cast<float2*>(ws + l.tn);
+  const int K = (int)d->n_bins, N1 = (int)d->band_bins;
+  const float2* X = reinterpret_cast<const float2*>(sfts);
+  // step 2 over all SFTs
+  if (d->median_window > 0) {
+    const size_t smem = (size_t)K * sizeof(float);
+    static int attr = 0;
+    if (!attr) {
+      if (cudaFuncSetAttribute(k_normalize, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxBins * 4) != cudaSuccess)
+        return FSTAT_ECUDA;
+      attr = 1;
+    }
+    k_normalize<<<(unsigned)n_sft, kFeThreads, smem, s>>>(X, xh, K, d->median_window);
+    X = xh;
+  }
+  static int attr1 = 0;
+  if (!attr1) {
+    if (cudaFuncSetAttribute(k_idft_n1, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kMaxN1 * 8) != cudaSuccess)
+      return FSTAT_ECUDA;
+    attr1 = 1;
+  }
+  const int ks0 = (int)(d->k_het - d->k_lo);
+  for (const Chunk1& c : ch) {
+    const int M = (int)c.m;
+    const int tmax = M > N1 ? M : N1;
+    k_tables<<<(tmax + 255) / 256, 256, 0, s>>>(tm, M, tn, N1);
+    const float2* Xc = X + c.a * K;
+    k_dft_alpha<<<dim3((K + 31) / 32, (M + 63) / 64), kFeThreads, 0, s>>>(Xc, K, M, tm, D);
+    k_merge<<<dim3((N1 + 255) / 256, M), kFeThreads, 0, s>>>(D, K, M, N1, ks0, d->dirichlet_terms, tm,
+                                                              d->tukey_frac / 2.0, Y);
+    k_idft_n1<<<dim3((N1 + kFeThreads * kOutPerThread - 1) / (kFeThreads * kOutPerThread), M), kFeThreads,
+                (size_t)2 * N1 * 8, s>>>(Y, N1, M, tn, U);
+    double cyc = f_h * (c.tc - t_start);
+    cyc -= floor(cyc);
+    const double n_tot = (double)N1 * (double)M;
+    k_idft_n2<<<dim3((N1 + 31) / 32, (M + kN2PerBlock - 1) / kN2PerBlock), kFeThreads, 0, s>>>(
+        U, N1, M, tm, (float)(1.0 / sqrt((double)M * n_tot)), (float)cos(2.0 * M_PI * cyc),
+        (float)(-sin(2.0 * M_PI * cyc)), d->edge_taper, c.off, reinterpret_cast<float2*>(x_h));
+  }
+  return cudaGetLastError() == cudaSuccess ? FSTAT_OK : FSTAT_ECUDA;
+}

@@ -49,7 +49,8 @@ def _c_layout():
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', 'int main(void){']
     for cname, cls in (("fstat_detector", _lib.Detector), ("fstat_ephem", _lib.Ephem),
                        ("fstat_plan_desc", _lib.PlanDesc), ("fstat_template", _lib.Template),
-                       ("fstat_tuning", _lib.Tuning), ("fstat_injection", _lib.Injection)):
+                       ("fstat_tuning", _lib.Tuning), ("fstat_injection", _lib.Injection),
+                       ("fstat_sft_desc", _lib.SftDesc)):
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
         for f, _ in cls._fields_:
             lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
@@ -70,7 +71,8 @@ def test_struct_layouts_match_header():
         got[(parts[0], parts[1])] = int(parts[2])
     for cname, cls in (("fstat_detector", _lib.Detector), ("fstat_ephem", _lib.Ephem),
                        ("fstat_plan_desc", _lib.PlanDesc), ("fstat_template", _lib.Template),
-                       ("fstat_tuning", _lib.Tuning), ("fstat_injection", _lib.Injection)):
+                       ("fstat_tuning", _lib.Tuning), ("fstat_injection", _lib.Injection),
+                       ("fstat_sft_desc", _lib.SftDesc)):
         assert got[(cname, "size")] == ctypes.sizeof(cls)
         for f, _ in cls._fields_:
             assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
@@ -112,6 +114,23 @@ def test_inject_rejects_bad_arguments_on_the_host(lib):
     """fstat_inject checks its plan, pointers and sizes before any launch."""
     assert lib.fstat_inject(None, None, 0, 0, None, None) == -1               # no plan
     assert lib.fstat_inject(None, None, 1, 86400, None, None) == -1
+
+
+def test_sft_front_end_checks_its_descriptor_on_the_host(lib):
+    """fstat_sft_workspace / fstat_sft_series validate the descriptor before
+    any device work (no GPU needed)."""
+    import synth
+    from paper_0912_4255_gb300 import _sft_desc
+    good = synth.SftDesc(sft_len=2048, k_lo=344, n_bins=112, k_het=400, band_bins=64, dirichlet_terms=16)
+    assert lib.fstat_sft_workspace(ctypes.byref(_sft_desc(good)), 10) > 0
+    for bad, code in [(dict(band_bins=63), -1), (dict(median_window=10), -1), (dict(dt_raw=0.0), -1),
+                      (dict(tukey_frac=1.5), -1), (dict(k_lo=360), -2), (dict(n_bins=90), -2),
+                      (dict(dirichlet_terms=-1), -1)]:
+        d = _sft_desc(good.replace(**bad))
+        assert lib.fstat_sft_workspace(ctypes.byref(d), 10) == 0
+        assert lib.fstat_sft_series(ctypes.byref(d), None, None, 0, 0.0, 0, None, None, 0, None) == code
+    d = _sft_desc(good)
+    assert lib.fstat_sft_series(ctypes.byref(d), None, None, 0, 0.0, 0, None, None, 0, None) == -1   # no output
 
 
 def test_injection_records_match_the_struct():
