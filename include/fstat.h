@@ -355,6 +355,40 @@ int fstat_sft_series(const fstat_sft_desc *d, const float *sfts, const double *t
                      double t_start, int64_t n_out, float *x_h, void *workspace, size_t ws_bytes,
                      void *stream);
 
+/* Step 2 of the front end alone: out = X / sqrt(S), S the running median of
+ * |X|^2 over median_window bins (odd, >= 1) divided by ln 2, per SFT; the
+ * normalised SFTs that fstat_sft_demod takes.  sfts, out: device complex64
+ * [n_sft][n_bins] (may be the same array only if no other work reads it
+ * meanwhile: every SFT is read whole before it is written).  Errors: EINVAL
+ * (null or misaligned pointers, bad window or n_bins), ECUDA. */
+int fstat_sft_normalize(const fstat_sft_desc *d, const float *sfts, int64_t n_sft, float *out, void *stream);
+
+/* The SFT-domain demodulation F-statistic, the earlier method of the paper's
+ * speed comparison (Sec. IV.A), derived from Eq. 7 with the phase linear and
+ * a, b constant within each SFT (midpoint values) and the SFT interpolated
+ * at the fractional bin kappa_alpha = fhat_alpha T_SFT by the Dirichlet
+ * kernel of Eq. e9 (2 dirichlet_terms + 1 terms):
+ *   F_a = sum_alpha a_alpha e^{-2 pi i (Phi_alpha / 2 pi - kappa_alpha / 2)}
+ *         sum_k X_{alpha,k} P(kappa_alpha - k),
+ * Phi the template phase of Eq. 4 (to s = 2) at the SFT midpoint, fhat its
+ * instantaneous frequency there; 2F = 2 (B |F_a|^2 + A |F_b|^2
+ * - 2 C Re F_a F_b*) / D with A = sum a^2, B = sum b^2, C = sum ab.  For the
+ * frequencies f_q = f_het + (q - n_fft/2) / (n_fft dt) of the plan's output
+ * grid, q0 <= q < q0 + n_q, of every template (alpha, delta, fdot, fddot;
+ * its span, gap and n_fft fields are not used: the SFTs are the data).
+ * sfts: device complex64 [n_sft][n_bins], normalised (fstat_sft_normalize)
+ * bins k_lo .. of the descriptor; t_sft: device float64 [n_sft] SFT start
+ * times; templates: device [n_t]; twoF: device float32 [n_t][n_q];
+ * workspace: device, 256-byte aligned, fstat_sft_demod_workspace bytes.  A
+ * frequency whose kernel terms leave the stored bins gets NaN and sets the
+ * plan's status (ERANGE); an invalid template, NaN and EINVAL.  Host errors:
+ * EINVAL (null or misaligned pointers, bad descriptor), ERANGE
+ * (n_t > 65535), ENOMEM (workspace too small), ECUDA. */
+size_t fstat_sft_demod_workspace(int64_t n_sft, int64_t n_t);
+int fstat_sft_demod(fstat_plan_t p, const fstat_sft_desc *d, const float *sfts, const double *t_sft, int64_t n_sft,
+                    const fstat_template *templates, int64_t n_t, int64_t q0, int64_t n_q, float *twoF,
+                    void *workspace, size_t ws_bytes, void *stream);
+
 /* Synchronise the stream, return and clear the first device-side error
  * recorded since the last call (FSTAT_OK if none). */
 int fstat_status(fstat_plan_t p, void *stream);

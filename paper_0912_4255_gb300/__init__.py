@@ -26,6 +26,7 @@ __all__ = [
     "fstat_status", "fstat_destroy", "fstat_strerror", "fstat_template_nb", "pack_templates",
     "fstat_profile", "fstat_profile_read", "KERNEL_KINDS", "GraphRunner", "fstat_debug_stall", "fstat_topk",
     "fstat_inject", "pack_injections", "INJECTION_DTYPE", "fstat_sft_series", "fstat_sft_workspace",
+    "fstat_sft_normalize", "fstat_sft_demod",
     "NEAREST", "SINC", "WIN_RECT", "WIN_LANCZOS", "PREC_MIXED", "PREC_FP64", "PREC_FP32",
     "MODE_FUSED", "MODE_PLAIN", "MODE_PERSISTENT", "MODE_SPLIT", "TEMPLATE_DTYPE",
 ]
@@ -302,6 +303,39 @@ def fstat_sft_series(desc, sfts, t_sft, t_start: float, n_out: int, x_h=None, wo
                                 ctypes.c_void_p(workspace.data_ptr() + off), workspace.numel() - off,
                                 _stream(stream)), "fstat_sft_series")
     return x_h
+
+
+def fstat_sft_normalize(desc, sfts, out=None, stream=None):
+    """Running-median noise normalisation of SFTs (device complex64
+    [n_sft, n_bins]); returns the normalised copy."""
+    import torch
+    assert sfts.is_cuda and sfts.dtype == torch.complex64 and sfts.is_contiguous()
+    out = torch.empty_like(sfts) if out is None else out
+    _check(_lib.load().fstat_sft_normalize(ctypes.byref(_sft_desc(desc)), _ptr(sfts), sfts.shape[0], _ptr(out),
+                                           _stream(stream)), "fstat_sft_normalize")
+    return out
+
+
+def fstat_sft_demod(plan: Plan, desc, sfts, t_sft, templates, q0: int, n_q: int, twoF=None, workspace=None,
+                    stream=None):
+    """SFT-domain demodulation 2F (the comparison method of Sec. IV.A) on
+    bins q0 .. q0 + n_q - 1 of the plan's output grid.  sfts: normalised,
+    device complex64 [n_sft, n_bins]; t_sft: device float64 [n_sft];
+    templates: device records.  Returns float32 [n_t, n_q]."""
+    import torch
+    n_t = _n_templates(templates)
+    n_sft = int(t_sft.numel())
+    if twoF is None:
+        twoF = torch.empty((n_t, int(n_q)), dtype=torch.float32, device=sfts.device)
+    need = int(plan.lib.fstat_sft_demod_workspace(n_sft, n_t))
+    if workspace is None or workspace.numel() < need + 256:
+        workspace = torch.empty(need + 256, dtype=torch.uint8, device=sfts.device)
+    off = (-workspace.data_ptr()) % 256
+    _check(plan.lib.fstat_sft_demod(plan.handle, ctypes.byref(_sft_desc(desc)), _ptr(sfts), _ptr(t_sft), n_sft,
+                                    _ptr(templates), n_t, int(q0), int(n_q), _ptr(twoF),
+                                    ctypes.c_void_p(workspace.data_ptr() + off), workspace.numel() - off,
+                                    _stream(stream)), "fstat_sft_demod")
+    return twoF
 
 
 def fstat_topk(two_f, band_len: int, k: int, n_rows: int | None = None, stream=None):

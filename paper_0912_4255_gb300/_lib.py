@@ -99,6 +99,10 @@ SYMBOLS = {
     "fstat_sft_workspace": (ctypes.c_size_t, [ctypes.POINTER(SftDesc), c_int64]),
     "fstat_sft_series": (ctypes.c_int, [ctypes.POINTER(SftDesc), c_void_p, ctypes.POINTER(c_double), c_int64,
                                         c_double, c_int64, c_void_p, c_void_p, ctypes.c_size_t, c_void_p]),
+    "fstat_sft_normalize": (ctypes.c_int, [ctypes.POINTER(SftDesc), c_void_p, c_int64, c_void_p, c_void_p]),
+    "fstat_sft_demod_workspace": (ctypes.c_size_t, [c_int64, c_int64]),
+    "fstat_sft_demod": (ctypes.c_int, [c_void_p, ctypes.POINTER(SftDesc), c_void_p, c_void_p, c_int64, c_void_p,
+                                       c_int64, c_int64, c_int64, c_void_p, c_void_p, ctypes.c_size_t, c_void_p]),
     "fstat_inject": (ctypes.c_int, [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_void_p]),
     "fstat_profile": (ctypes.c_int, [c_void_p, ctypes.c_int]),
     "fstat_profile_read": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int64),

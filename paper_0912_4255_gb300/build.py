@@ -37,7 +37,8 @@ def units():
            ("resample", "resample.cu", []), ("dispatch", "dispatch.cu", []),
            ("grad", "grad.cu", []), ("persist", "persist.cu", []),
            ("noalloc", "noalloc.cu", []), ("topk", "topk.cu", []),
-           ("inject", "inject.cu", []), ("frontend", "frontend.cu", [])]
+           ("inject", "inject.cu", []), ("frontend", "frontend.cu", []),
+           ("demod", "demod.cu", [])]
     for real in ("float", "double"):
         for L in LOGS:
             out.append((f"cols_{real}_{L}", "cols.cu", [f"-DFS_REAL={real}", f"-DFS_L1={L}"]))

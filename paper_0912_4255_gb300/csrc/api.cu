@@ -487,6 +487,32 @@ int fstat_profile_read(fstat_plan_t p, double* ms, int64_t* launches, int n_kind
   return rc;
 }
 
+size_t fstat_sft_demod_workspace(int64_t n_sft, int64_t n_t) {
+  if (n_sft < 0 || n_t < 0) return 0;
+  return demod_workspace(n_sft, n_t);
+}
+
+int fstat_sft_demod(fstat_plan_t p, const fstat_sft_desc* d, const float* sfts, const double* t_sft, int64_t n_sft,
+                    const fstat_template* templates, int64_t n_t, int64_t q0, int64_t n_q, float* twoF,
+                    void* workspace, size_t ws_bytes, void* stream) {
+  if (!p || !d) return FSTAT_EINVAL;
+  if (d->sft_len < 2 || !(d->dt_raw > 0.0) || d->n_bins < 1 || d->n_bins > (1 << 20) || d->dirichlet_terms < 0 ||
+      2 * (int64_t)d->dirichlet_terms + 1 > d->n_bins)
+    return FSTAT_EINVAL;
+  if (n_sft < 0 || n_t < 0 || n_q < 0 || n_sft > (1 << 24)) return FSTAT_EINVAL;
+  if (n_t > 65535) return FSTAT_ERANGE;
+  if (n_sft == 0 || n_t == 0 || n_q == 0) return FSTAT_OK;
+  if (!sfts || !t_sft || !templates || !twoF || !workspace || ((uintptr_t)sfts & 7) || ((uintptr_t)t_sft & 7) ||
+      ((uintptr_t)twoF & 3) || ((uintptr_t)workspace & 255))
+    return FSTAT_EINVAL;
+  if (ws_bytes < demod_workspace(n_sft, n_t)) return FSTAT_ENOMEM;
+  const double df = 1.0 / ((double)p->d.n_fft * p->d.dt);
+  const double f0 = p->d.f_het + (double)(q0 - p->d.n_fft / 2) * df;
+  const cudaError_t e = launch_demod(p->pc, *d, reinterpret_cast<const float2*>(sfts), t_sft, n_sft, templates, n_t,
+                                     f0, df, n_q, twoF, workspace, p->status, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? FSTAT_OK : FSTAT_ECUDA;
+}
+
 int fstat_set_band(fstat_plan_t p, int64_t q_lo, int64_t q_hi) {
   if (!p) return FSTAT_EINVAL;
   if (q_lo < 0 || q_hi <= q_lo || q_hi > p->d.n_fft) return FSTAT_ERANGE;

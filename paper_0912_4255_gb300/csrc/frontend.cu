@@ -300,6 +300,26 @@ int check(const fstat_sft_desc* d) {
 
 }  // namespace fs
 
+extern "C" int fstat_sft_normalize(const fstat_sft_desc* d, const float* sfts, int64_t n_sft, float* out,
+                                   void* stream) {
+  using namespace fs;
+  if (!d || d->n_bins < 1 || d->n_bins > kMaxBins || d->median_window < 1 || !(d->median_window & 1) ||
+      d->median_window > kMaxWindow || n_sft < 0)
+    return FSTAT_EINVAL;
+  if (n_sft == 0) return FSTAT_OK;
+  if (!sfts || !out || ((uintptr_t)sfts & 7) || ((uintptr_t)out & 7)) return FSTAT_EINVAL;
+  if (n_sft > 0x7fffffff) return FSTAT_ERANGE;
+  static int attr = 0;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_normalize, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxBins * 4) != cudaSuccess)
+      return FSTAT_ECUDA;
+    attr = 1;
+  }
+  k_normalize<<<(unsigned)n_sft, kFeThreads, (size_t)d->n_bins * 4, static_cast<cudaStream_t>(stream)>>>(
+      reinterpret_cast<const float2*>(sfts), reinterpret_cast<float2*>(out), (int)d->n_bins, d->median_window);
+  return cudaGetLastError() == cudaSuccess ? FSTAT_OK : FSTAT_ECUDA;
+}
+
 extern "C" size_t fstat_sft_workspace(const fstat_sft_desc* d, int64_t n_sft) {
   if (fs::check(d) != FSTAT_OK || n_sft < 0) return 0;
   return fs::layout(*d, n_sft > 0 ? n_sft : 1).total;

@@ -945,6 +945,10 @@ __host__ __device__ inline int default_log2_n1(int L) {
   return l1;
 }
 
+size_t demod_workspace(int64_t n_sft, int64_t n_t);
+cudaError_t launch_demod(const PlanConst& pc, const fstat_sft_desc& d, const float2* X, const double* t_sft,
+                         int64_t n_sft, const fstat_template* tm, int64_t n_t, double f0, double df, int64_t n_q,
+                         float* out, void* ws, int* status, cudaStream_t s);
 cudaError_t launch_inject(const PlanConst& pc, const fstat_injection* inj, int64_t n_inj, int64_t max_span,
                           float2* x, int* status, cudaStream_t s);
 cudaError_t launch_timemap(const PlanConst& pc, const Chunk& c, int log2n_plan, int mode,
