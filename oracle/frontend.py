@@ -12,8 +12,9 @@ data product of Eq. e25, X_{alpha,k} = sum_j x_{alpha,j} e^{-2 pi i j k / N}):
    median of an exponential variable is ln 2 times its mean), so that
    E|X^|^2 = 1 per bin; the window is truncated at the ends of the stored
    band and an even count takes its lower median;
-3. split the SFTs into contiguous runs (chunks): SFT alpha + 1 starts
-   exactly one SFT length after SFT alpha;
+3. split the SFTs into contiguous runs (chunks): SFT alpha + 1 starts one
+   SFT length after SFT alpha, to within 1e-6 of that length (a bin whose
+   noise estimate of step 2 is zero is set to zero);
 4. merge each chunk of M SFTs into the long time-baseline transform with
    the truncated Dirichlet kernel, Eq. e9:
      X_b = sum_alpha e^{-2 pi i b alpha / M}
@@ -58,19 +59,27 @@ def running_median_psd(X, w):
 
 
 def normalize(X, w):
-    """Eq. dimlessSFTs1 (w = 0: no normalisation)."""
+    """Eq. dimlessSFTs1 (w = 0: no normalisation).  A bin whose noise
+    estimate is zero (its window holds zeros only, e.g. an SFT of zeros)
+    carries no information and is set to zero."""
     X = np.asarray(X, np.complex128)
     if w == 0:
         return X.copy()
-    return X / np.sqrt(running_median_psd(X, w))
+    S = running_median_psd(X, w)
+    out = np.zeros_like(X)
+    ok = S > 0
+    out[ok] = X[ok] / np.sqrt(S[ok])
+    return out
 
 
-def chunks(t_sft, t_len, tol=1e-6):
-    """Contiguous runs of SFTs: list of (first index, count)."""
+def chunks(t_sft, t_len, rtol=1e-6):
+    """Contiguous runs of SFTs: list of (first index, count); SFT i + 1
+    continues the run when it starts T_SFT after SFT i to within
+    rtol T_SFT."""
     out = []
     a = 0
     for i in range(1, len(t_sft) + 1):
-        if i == len(t_sft) or abs(t_sft[i] - t_sft[i - 1] - t_len) > tol:
+        if i == len(t_sft) or abs(t_sft[i] - t_sft[i - 1] - t_len) > rtol * t_len:
             out.append((a, i - a))
             a = i
     return out

@@ -55,7 +55,8 @@ k_normalize(const float2* __restrict__ X, float2* __restrict__ Xh, int K, int w)
       }
       if (lt <= t && t < le) { med = v; break; }
     }
-    const float s = rsqrtf(med * 1.4426950408889634f);   // 1 / sqrt(median / ln 2)
+    // 1 / sqrt(median / ln 2); a zero estimate (a window of zeros) gives zero
+    const float s = med > 0.f ? rsqrtf(med * 1.4426950408889634f) : 0.f;
     const float2 v = x[k];
     y[k] = make_float2(v.x * s, v.y * s);
   }

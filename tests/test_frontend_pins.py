@@ -34,6 +34,15 @@ def test_dirichlet_kernel_special_values():
 def test_chunks_split_at_gaps_and_jitter():
     t = np.array([0, 1, 2, 5, 6, 7.5, 8.5]) * T_SFT
     assert FE.chunks(t, T_SFT) == [(0, 3), (3, 2), (5, 2)]
+    t = np.array([0, 1 + 5e-7, 2 + 5e-7, 3 + 3e-6]) * T_SFT       # within / beyond 1e-6 T_SFT
+    assert FE.chunks(t, T_SFT) == [(0, 3), (3, 1)]
+
+
+def test_zero_sfts_normalise_to_zero():
+    X = synth.sft_noise(3, 200, N, 1.0, 12).astype(np.complex128)
+    X[1] = 0.0
+    Xh = FE.normalize(X, 21)
+    assert np.all(Xh[1] == 0) and np.all(np.isfinite(Xh))
 
 
 def test_running_median_matches_brute_force_and_normalises():

@@ -56,6 +56,22 @@ def test_series_matches_the_oracle(kw):
     assert np.array_equal(got == 0, want == 0)          # gaps and the margins
 
 
+def test_zero_sft_and_jittered_times():
+    """An SFT of zeros normalises to zeros (no NaN), and start times
+    jittered by less than 1e-6 T_SFT still form one chunk, as in the
+    oracle."""
+    N = 2048
+    slots = [0, 1, 2, 3, 4, 5]
+    d, X, t = _case(N, 64, 16, 8, slots, 6, 77, median_window=33, tukey_frac=0.1)
+    X[2] = 0
+    t = t + np.array([0, 3e-7, -2e-7, 4e-7, 0, 1e-7]) * d.t_sft
+    n_out = 6 * 64
+    want = FE.sft_to_series(X.astype(np.complex128), t, d, 0.0, n_out)
+    got = _gpu(d, X, t, 0.0, n_out)
+    assert np.all(np.isfinite(got))
+    assert np.abs(got - want).max() < 3e-5 * np.abs(want).max()
+
+
 def test_bin_centred_sinusoids_at_full_band_size():
     """N1 = 3600 band bins per SFT (2 Hz at T_SFT = 1800 s: dt_out = 0.5 s),
     chunks of 24 and 9 SFTs: sinusoids with whole cycles per SFT come out
