@@ -11,8 +11,8 @@
 // length N_out = N1 M splits the same way (m = kappa M + r, n = n1 + N1 n2):
 //   z[n1 + N1 n2] = sum_r e^{2 pi i r n2 / M} e^{2 pi i r n1 / N_out}
 //                   sum_kappa Y[r][kappa] e^{2 pi i kappa n1 / N1},
-// two direct DFTs (k_idft_n1 over kappa, k_idft_n2 over r) with twiddle
-// indices taken exactly in integers.  The lengths (N1 = band bins per SFT,
+// two passes (k_idft_n1 over kappa, itself split as N1 = P Q, and
+// k_idft_n2 over r) with twiddle indices taken exactly in integers.  The lengths (N1 = band bins per SFT,
 // M = SFTs per chunk) are arbitrary, not powers of two.
 #include "fstat_internal.cuh"
 
@@ -26,7 +26,7 @@ namespace {
 
 constexpr int kFeThreads = 256;
 constexpr int kMaxBins = 32768;      // stored bins per SFT (running median in shared memory)
-constexpr int kMaxN1 = 8192;         // band bins per SFT (inverse pass over kappa in shared memory)
+constexpr int kMaxN1 = 8192;         // band bins per SFT (inverse pass over kappa: 3 rows in shared memory)
 constexpr int kMaxWindow = 1023;
 
 // Step 2: X^ = X / sqrt(S), S = (lower) median of |X|^2 over the window / ln 2.
@@ -60,6 +60,79 @@ k_normalize(const float2* __restrict__ X, float2* __restrict__ Xh, int K, int w)
     const float2 v = x[k];
     y[k] = make_float2(v.x * s, v.y * s);
   }
+}
+
+// The same normalisation with a sorted window per thread: each thread takes a
+// run of consecutive bins and slides its window along them (one removal and
+// one insertion per bin, O(w) instead of the O(w^2) counting above).  The
+// median picked is the same element of the same multiset.  Shared memory:
+// |X|^2 of the SFT, then one column of w values per thread ([j][thread]).
+constexpr int kSwBudget = 200 * 1024;  // bytes of shared memory this kernel may take
+__global__ void __launch_bounds__(kFeThreads)
+k_normalize_sw(const float2* __restrict__ X, float2* __restrict__ Xh, int K, int w) {
+  extern __shared__ float P[];
+  float* win = P + K;
+  const float2* x = X + (int64_t)blockIdx.x * K;
+  float2* y = Xh + (int64_t)blockIdx.x * K;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const float2 v = x[k];
+    P[k] = v.x * v.x + v.y * v.y;
+  }
+  __syncthreads();
+  const int h = w / 2;
+  const int run = (K + kFeThreads - 1) / kFeThreads;
+  const int k0 = threadIdx.x * run, k1 = min(K, k0 + run);
+  if (k0 >= k1) return;
+  float* wv = win + threadIdx.x;                // element j at wv[j * kFeThreads]
+  int cnt = 0;
+  auto insert = [&](float v) {
+    int j = cnt;
+    while (j > 0 && wv[(j - 1) * kFeThreads] > v) { wv[j * kFeThreads] = wv[(j - 1) * kFeThreads]; --j; }
+    wv[j * kFeThreads] = v;
+    ++cnt;
+  };
+  auto remove = [&](float v) {
+    int j = 0;
+    while (j < cnt - 1 && __float_as_int(wv[j * kFeThreads]) != __float_as_int(v)) ++j;
+    for (; j < cnt - 1; ++j) wv[j * kFeThreads] = wv[(j + 1) * kFeThreads];
+    --cnt;
+  };
+  for (int i = max(0, k0 - h); i < min(K, k0 + h + 1); ++i) insert(P[i]);
+  for (int k = k0; k < k1; ++k) {
+    if (k > k0) {
+      if (k - h - 1 >= 0) remove(P[k - h - 1]);
+      if (k + h < K) insert(P[k + h]);
+    }
+    const float med = wv[((cnt - 1) / 2) * kFeThreads];
+    const float s = med > 0.f ? rsqrtf(med * 1.4426950408889634f) : 0.f;
+    const float2 v = x[k];
+    y[k] = make_float2(v.x * s, v.y * s);
+  }
+}
+
+size_t normalize_sw_smem(int K, int w) { return ((size_t)K + (size_t)kFeThreads * (size_t)w) * sizeof(float); }
+
+// Step 2 on n_sft SFTs: the sliding-window kernel where it fits, else the
+// counting kernel.
+cudaError_t launch_normalize(const float2* X, float2* Xh, int64_t n_sft, int K, int w, cudaStream_t s) {
+  if (normalize_sw_smem(K, w) <= (size_t)kSwBudget) {
+    static int attr = 0;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_normalize_sw, cudaFuncAttributeMaxDynamicSharedMemorySize, kSwBudget);
+      if (e != cudaSuccess) return e;
+      attr = 1;
+    }
+    k_normalize_sw<<<(unsigned)n_sft, kFeThreads, normalize_sw_smem(K, w), s>>>(X, Xh, K, w);
+  } else {
+    static int attr = 0;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_normalize, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxBins * 4);
+      if (e != cudaSuccess) return e;
+      attr = 1;
+    }
+    k_normalize<<<(unsigned)n_sft, kFeThreads, (size_t)K * 4, s>>>(X, Xh, K, w);
+  }
+  return cudaGetLastError();
 }
 
 // Twiddle tables of one chunk: tm[j] = (cos, sin, 1 - cos) of 2 pi j / M,
@@ -156,50 +229,59 @@ k_merge(const float2* __restrict__ D, int K, int M, int N1, int ks0, int dk, con
 }
 
 // Step 5, first pass: U[r][n1] = e^{2 pi i r n1 / N_out} (-1)^{n1}
-// sum_{kp} Y[r][kp] e^{2 pi i kp n1 / N1}  (kp = kappa + N1/2).  One block per
-// r; the row of Y and the N1-table in shared memory; 4 outputs per thread.
-constexpr int kOutPerThread = 4;
+// sum_{kp} Y[r][kp] e^{2 pi i kp n1 / N1}  (kp = kappa + N1/2), as two short
+// DFTs with N1 = P Q (kp = Q k1 + k2, n1 = na + P nb):
+//   V[k2][na] = e^{2 pi i k2 na / N1} sum_{k1 < P} Y[Q k1 + k2] e^{2 pi i k1 na / P},
+//   sum = sum_{k2 < Q} V[k2][na] e^{2 pi i k2 nb / Q},
+// N1 (P + Q) products per r instead of N1^2.  The P- and Q-point twiddles
+// are every Q-th and P-th entry of the N1-table.  One block per r; the row
+// of Y, V and the table in shared memory.
 __global__ void __launch_bounds__(kFeThreads)
-k_idft_n1(const float2* __restrict__ Y, int N1, int M, const float2* __restrict__ tn, float2* __restrict__ U) {
+k_idft_n1(const float2* __restrict__ Y, int N1, int P, int M, const float2* __restrict__ tn, float2* __restrict__ U) {
   extern __shared__ float2 sm[];
   float2* ys = sm;
-  float2* ts = sm + N1;
-  const int r = blockIdx.y;
+  float2* vs = sm + N1;
+  float2* ts = sm + 2 * N1;
+  const int Q = N1 / P;
+  const int r = blockIdx.x;
   for (int i = threadIdx.x; i < N1; i += blockDim.x) {
     ys[i] = __ldg(Y + (int64_t)r * N1 + i);
     ts[i] = __ldg(tn + i);
   }
   __syncthreads();
-  const int base = blockIdx.x * (kFeThreads * kOutPerThread) + threadIdx.x;
-  float2 acc[kOutPerThread];
-  int idx[kOutPerThread], n1v[kOutPerThread];
-#pragma unroll
-  for (int q = 0; q < kOutPerThread; ++q) {
-    acc[q] = make_float2(0.f, 0.f);
-    idx[q] = 0;
-    n1v[q] = min(base + q * kFeThreads, N1 - 1);
-  }
-  for (int kp = 0; kp < N1; ++kp) {
-    const float2 y = ys[kp];
-#pragma unroll
-    for (int q = 0; q < kOutPerThread; ++q) {
-      const float2 t = ts[idx[q]];
-      acc[q].x += y.x * t.x - y.y * t.y;
-      acc[q].y += y.x * t.y + y.y * t.x;
-      idx[q] += n1v[q];                       // (kp n1) mod N1
-      if (idx[q] >= N1) idx[q] -= N1;
+  for (int i = threadIdx.x; i < N1; i += blockDim.x) {
+    const int k2 = i / P, na = i - k2 * P;
+    float2 acc = make_float2(0.f, 0.f);
+    int idx = 0;                                   // (k1 na) mod P
+    for (int k1 = 0; k1 < P; ++k1) {
+      const float2 y = ys[Q * k1 + k2], t = ts[idx * Q];
+      acc.x += y.x * t.x - y.y * t.y;
+      acc.y += y.x * t.y + y.y * t.x;
+      idx += na;
+      if (idx >= P) idx -= P;
     }
+    const float2 t = ts[k2 * na];                  // k2 na < N1
+    vs[i] = make_float2(acc.x * t.x - acc.y * t.y, acc.x * t.y + acc.y * t.x);
   }
+  __syncthreads();
   const int64_t n_out = (int64_t)N1 * M;
-#pragma unroll
-  for (int q = 0; q < kOutPerThread; ++q) {
-    const int n1 = base + q * kFeThreads;
-    if (n1 >= N1) continue;
+  for (int i = threadIdx.x; i < N1; i += blockDim.x) {
+    const int nb = i / P, na = i - nb * P;
+    const int n1 = na + P * nb;
+    float2 acc = make_float2(0.f, 0.f);
+    int idx = 0;                                   // (k2 nb) mod Q
+    for (int k2 = 0; k2 < Q; ++k2) {
+      const float2 v = vs[k2 * P + na], t = ts[idx * P];
+      acc.x += v.x * t.x - v.y * t.y;
+      acc.y += v.x * t.y + v.y * t.x;
+      idx += nb;
+      if (idx >= Q) idx -= Q;
+    }
     double s, c;
     sincospi(2.0 * (double)(((int64_t)r * n1) % n_out) / (double)n_out, &s, &c);
-    const float sg = (n1 & 1) ? -1.f : 1.f;  // e^{-pi i n1} from kappa = kp - N1/2
+    const float sg = (n1 & 1) ? -1.f : 1.f;      // e^{-pi i n1} from kappa = kp - N1/2
     const float cs = (float)c * sg, sn = (float)s * sg;
-    U[(int64_t)r * N1 + n1] = make_float2(acc[q].x * cs - acc[q].y * sn, acc[q].x * sn + acc[q].y * cs);
+    U[(int64_t)r * N1 + n1] = make_float2(acc.x * cs - acc.y * sn, acc.x * sn + acc.y * cs);
   }
 }
 
@@ -310,15 +392,9 @@ extern "C" int fstat_sft_normalize(const fstat_sft_desc* d, const float* sfts, i
   if (n_sft == 0) return FSTAT_OK;
   if (!sfts || !out || ((uintptr_t)sfts & 7) || ((uintptr_t)out & 7)) return FSTAT_EINVAL;
   if (n_sft > 0x7fffffff) return FSTAT_ERANGE;
-  static int attr = 0;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_normalize, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxBins * 4) != cudaSuccess)
-      return FSTAT_ECUDA;
-    attr = 1;
-  }
-  k_normalize<<<(unsigned)n_sft, kFeThreads, (size_t)d->n_bins * 4, static_cast<cudaStream_t>(stream)>>>(
-      reinterpret_cast<const float2*>(sfts), reinterpret_cast<float2*>(out), (int)d->n_bins, d->median_window);
-  return cudaGetLastError() == cudaSuccess ? FSTAT_OK : FSTAT_ECUDA;
+  return launch_normalize(reinterpret_cast<const float2*>(sfts), reinterpret_cast<float2*>(out), n_sft,
+                          (int)d->n_bins, d->median_window, static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? FSTAT_OK : FSTAT_ECUDA;
 }
 
 extern "C" size_t fstat_sft_workspace(const fstat_sft_desc* d, int64_t n_sft) {
@@ -368,22 +444,20 @@ extern "C" int fstat_sft_series(const fstat_sft_desc* d, const float* sfts, cons
   const float2* X = reinterpret_cast<const float2*>(sfts);
   // step 2 over all SFTs
   if (d->median_window > 0) {
-    const size_t smem = (size_t)K * sizeof(float);
-    static int attr = 0;
-    if (!attr) {
-      if (cudaFuncSetAttribute(k_normalize, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxBins * 4) != cudaSuccess)
-        return FSTAT_ECUDA;
-      attr = 1;
-    }
-    k_normalize<<<(unsigned)n_sft, kFeThreads, smem, s>>>(X, xh, K, d->median_window);
+    if (n_sft > 0x7fffffff || launch_normalize(X, xh, n_sft, K, d->median_window, s) != cudaSuccess)
+      return FSTAT_ECUDA;
     X = xh;
   }
   static int attr1 = 0;
   if (!attr1) {
-    if (cudaFuncSetAttribute(k_idft_n1, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kMaxN1 * 8) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_idft_n1, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * kMaxN1 * 8) != cudaSuccess)
       return FSTAT_ECUDA;
     attr1 = 1;
   }
+  // N1 = P Q with P the largest divisor of N1 not above sqrt(N1)
+  int P = 1;
+  for (int q = 1; (int64_t)q * q <= N1; ++q)
+    if (N1 % q == 0) P = q;
   const int ks0 = (int)(d->k_het - d->k_lo);
   for (const Chunk1& c : ch) {
     const int M = (int)c.m;
@@ -393,8 +467,7 @@ extern "C" int fstat_sft_series(const fstat_sft_desc* d, const float* sfts, cons
     k_dft_alpha<<<dim3((K + 31) / 32, (M + 63) / 64), kFeThreads, 0, s>>>(Xc, K, M, tm, D);
     k_merge<<<dim3((N1 + 255) / 256, M), kFeThreads, 0, s>>>(D, K, M, N1, ks0, d->dirichlet_terms, tm,
                                                               d->tukey_frac / 2.0, Y);
-    k_idft_n1<<<dim3((N1 + kFeThreads * kOutPerThread - 1) / (kFeThreads * kOutPerThread), M), kFeThreads,
-                (size_t)2 * N1 * 8, s>>>(Y, N1, M, tn, U);
+    k_idft_n1<<<(unsigned)M, kFeThreads, (size_t)3 * N1 * 8, s>>>(Y, N1, P, M, tn, U);
     double cyc = f_h * (c.tc - t_start);
     cyc -= floor(cyc);
     const double n_tot = (double)N1 * (double)M;
