@@ -89,3 +89,13 @@ def test_demodulation_argument_errors():
     tm = fs.pack_templates(synth.make_templates([1.0], [0.2], [0.0], 0, 1), device="cuda")
     with pytest.raises(fs.FstatError):                  # 2 dk + 1 > n_bins
         fs.fstat_sft_demod(p, sd, X, t, tm, 0, 16)
+
+
+def test_no_bins_or_templates_is_a_no_op():
+    import torch
+    import paper_0912_4255_gb300 as fs
+    X, t_sft, plan, sd, inj, q_off = _data()
+    p = fs.Plan(plan, device=torch.device("cuda:0"))
+    tm = fs.pack_templates(synth.make_templates([1.0], [0.2], [0.0], 0, 1), device="cuda")
+    out = fs.fstat_sft_demod(p, sd, torch.from_numpy(X).cuda(), torch.from_numpy(t_sft).cuda(), tm, 100, 0)
+    assert out.numel() == 0 and fs.fstat_status(p, raise_error=False) == 0

@@ -99,3 +99,13 @@ def test_bin_centred_sinusoids_at_full_band_size():
     scale = np.abs(want).max()
     assert np.abs(got[inside] - want[inside]).max() < 2e-4 * scale
     assert np.all(got[~inside] == 0)
+
+
+def test_no_sfts_gives_zeros():
+    import torch
+    import paper_0912_4255_gb300 as fs
+    d, X, t = _case(2048, 64, 16, 8, [0], 1, 5)
+    x = torch.full((300,), 7.0, dtype=torch.complex64, device="cuda")
+    fs.fstat_sft_series(d, torch.from_numpy(X[:0].copy()).cuda(), t[:0], 0.0, 300, x_h=x)
+    torch.cuda.synchronize()
+    assert bool((x == 0).all())

@@ -106,3 +106,15 @@ def test_injected_signal_through_the_path():
     assert err < 1e-4, err
     q = desc.n_fft // 2 + 3000
     assert want[q] > 300 and int(np.argmax(out)) == q
+
+
+def test_no_injections_is_a_no_op():
+    import torch
+    import paper_0912_4255_gb300 as fs
+    desc = synth.tiny_plan(n_data=1000)
+    plan = _plan(desc)
+    x = torch.ones(desc.n_data, dtype=torch.complex64, device="cuda:0")
+    fs.fstat_inject(plan, x, synth.injection_records([], 1.0, 0, 0))
+    fs.fstat_inject(plan, x, synth.injection_records(_injections()[:1], 1.0, 0, 0))   # empty span
+    assert fs.fstat_status(plan, raise_error=False) == 0
+    assert bool((x == 1).all())
