@@ -135,32 +135,69 @@ cudaError_t launch_normalize(const float2* X, float2* Xh, int64_t n_sft, int K, 
   return cudaGetLastError();
 }
 
-// Twiddle tables of one chunk: tm[j] = (cos, sin, 1 - cos) of 2 pi j / M,
-// tn[j] = (cos, sin) of 2 pi j / N1, from FP64.
-__global__ void k_tables(float4* __restrict__ tm, int M, float2* __restrict__ tn, int N1) {
+// The chunks of one launch (passed by value: no copy to the device, and a
+// captured launch keeps its own table).  Chunks partition consecutive SFTs,
+// so every per-SFT row (of D, Y, U and the M-tables) is addressed by its
+// global SFT index g; chunk c holds rows a[c] .. a[c] + m[c] - 1.
+constexpr int kChunksPerLaunch = 32;
+constexpr int kN2PerBlock = 64;        // y-blocks of k_dft_alpha and k_idft_n2 cover 64 r or n2 each
+struct ChunkTab {
+  int n;                               // chunks in this launch
+  int rows;                            // SFTs they hold: a[0] .. a[0] + rows - 1
+  int a[kChunksPerLaunch], m[kChunksPerLaunch];
+  int yb[kChunksPerLaunch + 1];        // prefix sums of ceil(m / 64)
+  long long off[kChunksPerLaunch];     // output offset of the chunk
+  float gc[kChunksPerLaunch], gs[kChunksPerLaunch];   // chunk factor e^{-2 pi i f_h (t_c - t_s)}
+  float sc[kChunksPerLaunch];          // 1 / sqrt(M N_out)
+};
+
+__device__ __forceinline__ int chunk_of_row(const ChunkTab& t, int g) {
+  int c = 0;
+  while (c + 1 < t.n && g >= t.a[c] + t.m[c]) ++c;
+  return c;
+}
+__device__ __forceinline__ int chunk_of_yblock(const ChunkTab& t, int y) {
+  int c = 0;
+  while (c + 1 < t.n && y >= t.yb[c + 1]) ++c;
+  return c;
+}
+
+// Twiddle tables: tm[g] = (cos, sin, 1 - cos) of 2 pi j / M for row g = a + j
+// of a chunk of M SFTs, tn[j] = (cos, sin) of 2 pi j / N1, from FP64.
+__global__ void k_tables(ChunkTab tab, float4* __restrict__ tm, float2* __restrict__ tn, int N1) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < M) {
-    double s, c, sh, ch;
-    sincospi(2.0 * i / M, &s, &c);
-    sincospi((double)i / M, &sh, &ch);
-    tm[i] = make_float4((float)c, (float)s, (float)(2.0 * sh * sh), 0.f);
+  if (i < tab.rows) {
+    const int g = tab.a[0] + i;
+    const int c = chunk_of_row(tab, g);
+    const int j = g - tab.a[c], M = tab.m[c];
+    double s, co, sh, ch;
+    sincospi(2.0 * j / M, &s, &co);
+    sincospi((double)j / M, &sh, &ch);
+    tm[g] = make_float4((float)co, (float)s, (float)(2.0 * sh * sh), 0.f);
   }
   if (i < N1) {
-    double s, c;
-    sincospi(2.0 * i / N1, &s, &c);
-    tn[i] = make_float2((float)c, (float)s);
+    double s, co;
+    sincospi(2.0 * i / N1, &s, &co);
+    tn[i] = make_float2((float)co, (float)s);
   }
 }
 
-// Step 4a: D[r][k] = sum_alpha Xh[alpha][k] e^{-2 pi i r alpha / M}.  Lanes
-// run over k (coalesced rows of Xh); every warp owns 8 consecutive r, whose
-// twiddles are the same for all its lanes.  grid (ceil(K / 32), ceil(M / 64)).
+// Step 4a: D[r][k] = sum_alpha Xh[alpha][k] e^{-2 pi i r alpha / M} per
+// chunk (rows a + r of D).  Lanes run over k (coalesced rows of Xh); every
+// warp owns 8 consecutive r, whose twiddles are the same for all its lanes.
+// grid (ceil(K / 32), yb[n]).
 constexpr int kRPerWarp = 8;
 __global__ void __launch_bounds__(kFeThreads)
-k_dft_alpha(const float2* __restrict__ Xh, int K, int M, const float4* __restrict__ tm, float2* __restrict__ D) {
+k_dft_alpha(ChunkTab tab, const float2* __restrict__ Xh0, int K, const float4* __restrict__ tm0,
+            float2* __restrict__ D0) {
+  const int ch = chunk_of_yblock(tab, blockIdx.y);
+  const int M = tab.m[ch];
+  const float2* Xh = Xh0 + (int64_t)tab.a[ch] * K;
+  const float4* tm = tm0 + tab.a[ch];
+  float2* D = D0 + (int64_t)tab.a[ch] * K;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int k = blockIdx.x * 32 + lane;
-  const int r0 = (blockIdx.y * (kFeThreads / 32) + warp) * kRPerWarp;
+  const int r0 = ((blockIdx.y - tab.yb[ch]) * (kFeThreads / 32) + warp) * kRPerWarp;
   if (r0 >= M) return;
   float2 acc[kRPerWarp];
   int idx[kRPerWarp], step[kRPerWarp];
@@ -190,16 +227,21 @@ k_dft_alpha(const float2* __restrict__ Xh, int K, int M, const float4* __restric
 
 // Step 4b + the Tukey window of step 5: for m = kappa M + r,
 // Y[r][kappa + N1/2] = w_m sum_{j=-dk}^{dk} P(r, j) D[r][k_s + j],
-// k_s = k_het - k_lo + kappa.  grid (ceil(N1 / 256), M).
+// k_s = k_het - k_lo + kappa (rows a + r of D and Y).  grid (ceil(N1 / 256), rows).
 __global__ void __launch_bounds__(kFeThreads)
-k_merge(const float2* __restrict__ D, int K, int M, int N1, int ks0, int dk, const float4* __restrict__ tm,
-        double tukey_e, float2* __restrict__ Y) {
-  const int r = blockIdx.y;
+k_merge(ChunkTab tab, const float2* __restrict__ D, int K, int N1, int ks0, int dk, const float4* __restrict__ tm0,
+        double tukey_e, float2* __restrict__ Y0) {
+  const int g = tab.a[0] + blockIdx.y;
+  const int ch = chunk_of_row(tab, g);
+  const int M = tab.m[ch];
+  const int r = g - tab.a[ch];
+  const float4* tm = tm0 + tab.a[ch];
+  float2* Y = Y0 + (int64_t)tab.a[ch] * N1;
   const int kp = blockIdx.x * blockDim.x + threadIdx.x;      // kappa + N1/2
   if (kp >= N1) return;
   const int kappa = kp - N1 / 2;
   const int ks = ks0 + kappa;
-  const float2* d = D + (int64_t)r * K;
+  const float2* d = D + (int64_t)g * K;
   float2 acc;
   if (r == 0) {
     acc = __ldg(d + ks);                      // y = 0 only at j = 0; P = 0 at the other SFT bins
@@ -237,15 +279,19 @@ k_merge(const float2* __restrict__ D, int K, int M, int N1, int ks0, int dk, con
 // are every Q-th and P-th entry of the N1-table.  One block per r; the row
 // of Y, V and the table in shared memory.
 __global__ void __launch_bounds__(kFeThreads)
-k_idft_n1(const float2* __restrict__ Y, int N1, int P, int M, const float2* __restrict__ tn, float2* __restrict__ U) {
+k_idft_n1(ChunkTab tab, const float2* __restrict__ Y, int N1, int P, const float2* __restrict__ tn,
+          float2* __restrict__ U) {
   extern __shared__ float2 sm[];
   float2* ys = sm;
   float2* vs = sm + N1;
   float2* ts = sm + 2 * N1;
   const int Q = N1 / P;
-  const int r = blockIdx.x;
+  const int g = tab.a[0] + blockIdx.x;          // global row; r within its chunk
+  const int ch = chunk_of_row(tab, g);
+  const int M = tab.m[ch];
+  const int r = g - tab.a[ch];
   for (int i = threadIdx.x; i < N1; i += blockDim.x) {
-    ys[i] = __ldg(Y + (int64_t)r * N1 + i);
+    ys[i] = __ldg(Y + (int64_t)g * N1 + i);
     ts[i] = __ldg(tn + i);
   }
   __syncthreads();
@@ -281,7 +327,7 @@ k_idft_n1(const float2* __restrict__ Y, int N1, int P, int M, const float2* __re
     sincospi(2.0 * (double)(((int64_t)r * n1) % n_out) / (double)n_out, &s, &c);
     const float sg = (n1 & 1) ? -1.f : 1.f;      // e^{-pi i n1} from kappa = kp - N1/2
     const float cs = (float)c * sg, sn = (float)s * sg;
-    U[(int64_t)r * N1 + n1] = make_float2(acc.x * cs - acc.y * sn, acc.x * sn + acc.y * cs);
+    U[(int64_t)g * N1 + n1] = make_float2(acc.x * cs - acc.y * sn, acc.x * sn + acc.y * cs);
   }
 }
 
@@ -291,15 +337,20 @@ k_idft_n1(const float2* __restrict__ Y, int N1, int P, int M, const float2* __re
 // its own n2 values (warp-uniform twiddles); U staged in shared memory in
 // tiles of 64 r.  grid (ceil(N1 / 32), ceil(M / 64)).
 constexpr int kRTile = 64;
-constexpr int kN2PerBlock = 64;
 __global__ void __launch_bounds__(kFeThreads)
-k_idft_n2(const float2* __restrict__ U, int N1, int M, const float4* __restrict__ tm, float scale, float gc,
-          float gs, int64_t taper, int64_t off, float2* __restrict__ x) {
+k_idft_n2(ChunkTab tab, const float2* __restrict__ U0, int N1, const float4* __restrict__ tm0, int64_t taper,
+          float2* __restrict__ x) {
   __shared__ float2 us[kRTile][32];
+  const int ch = chunk_of_yblock(tab, blockIdx.y);
+  const int M = tab.m[ch];
+  const float2* U = U0 + (int64_t)tab.a[ch] * N1;
+  const float4* tm = tm0 + tab.a[ch];
+  const float scale = tab.sc[ch], gc = tab.gc[ch], gs = tab.gs[ch];
+  const int64_t off = tab.off[ch];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int n1 = blockIdx.x * 32 + lane;
   constexpr int PER_WARP = kN2PerBlock / (kFeThreads / 32);
-  const int n2_0 = blockIdx.y * kN2PerBlock + warp * PER_WARP;
+  const int n2_0 = (blockIdx.y - tab.yb[ch]) * kN2PerBlock + warp * PER_WARP;
   float2 acc[PER_WARP];
   int idx[PER_WARP], step[PER_WARP];
 #pragma unroll
@@ -459,21 +510,38 @@ extern "C" int fstat_sft_series(const fstat_sft_desc* d, const float* sfts, cons
   for (int q = 1; (int64_t)q * q <= N1; ++q)
     if (N1 % q == 0) P = q;
   const int ks0 = (int)(d->k_het - d->k_lo);
-  for (const Chunk1& c : ch) {
-    const int M = (int)c.m;
-    const int tmax = M > N1 ? M : N1;
-    k_tables<<<(tmax + 255) / 256, 256, 0, s>>>(tm, M, tn, N1);
-    const float2* Xc = X + c.a * K;
-    k_dft_alpha<<<dim3((K + 31) / 32, (M + 63) / 64), kFeThreads, 0, s>>>(Xc, K, M, tm, D);
-    k_merge<<<dim3((N1 + 255) / 256, M), kFeThreads, 0, s>>>(D, K, M, N1, ks0, d->dirichlet_terms, tm,
-                                                              d->tukey_frac / 2.0, Y);
-    k_idft_n1<<<(unsigned)M, kFeThreads, (size_t)3 * N1 * 8, s>>>(Y, N1, P, M, tn, U);
-    double cyc = f_h * (c.tc - t_start);
-    cyc -= floor(cyc);
-    const double n_tot = (double)N1 * (double)M;
-    k_idft_n2<<<dim3((N1 + 31) / 32, (M + kN2PerBlock - 1) / kN2PerBlock), kFeThreads, 0, s>>>(
-        U, N1, M, tm, (float)(1.0 / sqrt((double)M * n_tot)), (float)cos(2.0 * M_PI * cyc),
-        (float)(-sin(2.0 * M_PI * cyc)), d->edge_taper, c.off, reinterpret_cast<float2*>(x_h));
+  // the chunks in groups of at most kChunksPerLaunch chunks and 65535 SFTs
+  // (grid y of k_merge): 5 launches per group
+  for (size_t c0 = 0; c0 < ch.size();) {
+    ChunkTab tab;
+    int64_t rows = 0;
+    tab.n = 0;
+    while (c0 + tab.n < ch.size() && tab.n < kChunksPerLaunch && rows + ch[c0 + tab.n].m <= 65535)
+      rows += ch[c0 + tab.n++].m;
+    tab.yb[0] = 0;
+    for (int i = 0; i < tab.n; ++i) {
+      const Chunk1& c = ch[c0 + i];
+      tab.a[i] = (int)c.a;
+      tab.m[i] = (int)c.m;
+      tab.yb[i + 1] = tab.yb[i] + (int)((c.m + kN2PerBlock - 1) / kN2PerBlock);
+      tab.off[i] = c.off;
+      double cyc = f_h * (c.tc - t_start);
+      cyc -= floor(cyc);
+      tab.gc[i] = (float)cos(2.0 * M_PI * cyc);
+      tab.gs[i] = (float)(-sin(2.0 * M_PI * cyc));
+      tab.sc[i] = (float)(1.0 / sqrt((double)c.m * ((double)N1 * (double)c.m)));
+    }
+    for (int i = tab.n; i < kChunksPerLaunch; ++i) { tab.a[i] = tab.m[i] = 0; tab.yb[i + 1] = tab.yb[tab.n]; }
+    tab.rows = (int)(ch[c0 + tab.n - 1].a + ch[c0 + tab.n - 1].m - ch[c0].a);
+    const int tmax = tab.rows > N1 ? tab.rows : N1;
+    k_tables<<<(tmax + 255) / 256, 256, 0, s>>>(tab, tm, tn, N1);
+    k_dft_alpha<<<dim3((K + 31) / 32, tab.yb[tab.n]), kFeThreads, 0, s>>>(tab, X, K, tm, D);
+    k_merge<<<dim3((N1 + 255) / 256, tab.rows), kFeThreads, 0, s>>>(tab, D, K, N1, ks0, d->dirichlet_terms, tm,
+                                                                    d->tukey_frac / 2.0, Y);
+    k_idft_n1<<<(unsigned)tab.rows, kFeThreads, (size_t)3 * N1 * 8, s>>>(tab, Y, N1, P, tn, U);
+    k_idft_n2<<<dim3((N1 + 31) / 32, tab.yb[tab.n]), kFeThreads, 0, s>>>(tab, U, N1, tm, d->edge_taper,
+                                                                          reinterpret_cast<float2*>(x_h));
+    c0 += tab.n;
   }
   return cudaGetLastError() == cudaSuccess ? FSTAT_OK : FSTAT_ECUDA;
 }
