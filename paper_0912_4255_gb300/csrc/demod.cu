@@ -137,22 +137,25 @@ k_demod(const DemodRec* __restrict__ rec, const double* __restrict__ abc, const 
       // 44 bits could round up to 1.0 and put y = 0 on the next kernel term)
       const float fr = (float)((rel & ((1ll << kFracBits) - 1)) >> (kFracBits - 24)) * kInv24;
       if (kst - dk < 0 || kst + dk >= K) { bad = 2; continue; }
-      float s1, c1;
-      sincospif(fr, &s1, &c1);
-      const float siny = 2.f * s1 * c1, omc = 2.f * s1 * s1;   // sin y, 1 - cos y (y = 2 pi (fr - j))
       const float2* xr = X + (int64_t)(a0 + i) * K + kst;
-      float2 S = make_float2(0.f, 0.f);
-      for (int j = -dk; j <= dk; ++j) {
-        const float2 v = __ldg(xr + j);
-        float pr, pi;
-        if (j == 0 && fr == 0.f) {
-          pr = 1.f; pi = 0.f;
-        } else {
-          const float iy = 1.0f / (6.283185307179586f * (fr - (float)j));
-          pr = siny * iy; pi = -omc * iy;
+      float2 S;
+      if (fr == 0.f) {
+        S = __ldg(xr);                              // y = 0 at j = 0, P = 0 at the other terms
+      } else {
+        // sin y and 1 - cos y are the same for every term (y = 2 pi (fr - j)),
+        // so S = (sin y - i (1 - cos y)) / 2 pi * sum_j X_j / (fr - j)
+        float2 T = make_float2(0.f, 0.f);
+        for (int j = -dk; j <= dk; ++j) {
+          const float2 v = __ldg(xr + j);
+          const float iv = rcp_approx(fr - (float)j);
+          T.x = fmaf(v.x, iv, T.x);
+          T.y = fmaf(v.y, iv, T.y);
         }
-        S.x += v.x * pr - v.y * pi;
-        S.y += v.x * pi + v.y * pr;
+        float s1, c1;
+        sincospif(fr, &s1, &c1);
+        const float pr = 2.f * s1 * c1 * 0.15915494309189535f;   // sin y / 2 pi
+        const float pi = -2.f * s1 * s1 * 0.15915494309189535f;  // -(1 - cos y) / 2 pi
+        S = make_float2(T.x * pr - T.y * pi, T.x * pi + T.y * pr);
       }
       const unsigned long long ph = r.ph0 + (unsigned long long)qq * r.dph;
       const float ang = (float)(ph >> 40) * 5.9604644775390625e-8f;   // 2^-24 cycles
