@@ -22,22 +22,12 @@ cudaError_t run(const ColsArgs<R>& a, dim3 grid, cudaStream_t s) {
   constexpr int NT = threads_for<R>(L1, 2 * C);
   constexpr size_t SM = cols_smem<R, L1, C>();
   auto kern = k_cols<R, L1, C, NT, SRC, TAPS>;
-  static int attr_done = 0;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM);
-    if (e != cudaSuccess) return e;
-    attr_done = 1;
-  }
   // persistent grid: the blocks that fit on the device at once
-  static int resident = 0;
-  if (!resident) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, SM);
-    if (e != cudaSuccess) return e;
-    resident = sms * (per_sm > 0 ? per_sm : 1);
-  }
+  static DeviceOnce once;
+  int resident = 0;
+  const cudaError_t e = kernel_setup(once, kern, NT, SM, &resident);
+  if (e != cudaSuccess) return e;
+  if (resident < 1) resident = 1;
   // (the fused resampling source keeps one tile per block: its gathers run
   // slower when blocks drift apart)
   const unsigned total = grid.x * grid.y;

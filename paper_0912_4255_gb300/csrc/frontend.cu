@@ -116,20 +116,14 @@ size_t normalize_sw_smem(int K, int w) { return ((size_t)K + (size_t)kFeThreads 
 // counting kernel.
 cudaError_t launch_normalize(const float2* X, float2* Xh, int64_t n_sft, int K, int w, cudaStream_t s) {
   if (normalize_sw_smem(K, w) <= (size_t)kSwBudget) {
-    static int attr = 0;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_normalize_sw, cudaFuncAttributeMaxDynamicSharedMemorySize, kSwBudget);
-      if (e != cudaSuccess) return e;
-      attr = 1;
-    }
+    static DeviceOnce once;
+    cudaError_t e = kernel_setup(once, k_normalize_sw, kFeThreads, kSwBudget, nullptr);
+    if (e != cudaSuccess) return e;
     k_normalize_sw<<<(unsigned)n_sft, kFeThreads, normalize_sw_smem(K, w), s>>>(X, Xh, K, w);
   } else {
-    static int attr = 0;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_normalize, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxBins * 4);
-      if (e != cudaSuccess) return e;
-      attr = 1;
-    }
+    static DeviceOnce once;
+    cudaError_t e = kernel_setup(once, k_normalize, kFeThreads, (size_t)kMaxBins * 4, nullptr);
+    if (e != cudaSuccess) return e;
     k_normalize<<<(unsigned)n_sft, kFeThreads, (size_t)K * 4, s>>>(X, Xh, K, w);
   }
   return cudaGetLastError();
@@ -499,12 +493,8 @@ extern "C" int fstat_sft_series(const fstat_sft_desc* d, const float* sfts, cons
       return FSTAT_ECUDA;
     X = xh;
   }
-  static int attr1 = 0;
-  if (!attr1) {
-    if (cudaFuncSetAttribute(k_idft_n1, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * kMaxN1 * 8) != cudaSuccess)
-      return FSTAT_ECUDA;
-    attr1 = 1;
-  }
+  static DeviceOnce once_n1;
+  if (kernel_setup(once_n1, k_idft_n1, kFeThreads, (size_t)3 * kMaxN1 * 8, nullptr) != cudaSuccess) return FSTAT_ECUDA;
   // N1 = P Q with P the largest divisor of N1 not above sqrt(N1)
   int P = 1;
   for (int q = 1; (int64_t)q * q <= N1; ++q)

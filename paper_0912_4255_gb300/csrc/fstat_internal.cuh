@@ -7,6 +7,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <type_traits>
 
 #include "../../include/fstat.h"
@@ -97,6 +98,49 @@ template <typename R> struct Tw {
   const cpx<R>* tl[kMaxLog + 1];
   const cpx<R>* th[kMaxLog + 1];
 };
+
+// ---------------------------------------------------------------- launch settings
+// Kernel attributes and the persistent grid sizes derived from them belong
+// to a device, and a process may drive several GPUs: they are applied and
+// cached per device (the current one at the call; devices 0..63).
+constexpr int kMaxDevices = 64;
+struct DeviceOnce {
+  std::atomic<unsigned long long> done{0};
+  std::atomic<int> value[kMaxDevices] = {};
+};
+
+// Runs set(dev, &v) once for the current device and returns its v in *out.
+template <typename F>
+inline cudaError_t device_once(DeviceOnce& o, int* out, F&& set) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  const unsigned long long bit = 1ull << dev;
+  if (!(o.done.load(std::memory_order_acquire) & bit)) {
+    int v = 0;
+    e = set(dev, &v);
+    if (e != cudaSuccess) return e;
+    o.value[dev].store(v, std::memory_order_relaxed);
+    o.done.fetch_or(bit, std::memory_order_release);
+  }
+  if (out) *out = o.value[dev].load(std::memory_order_relaxed);
+  return cudaSuccess;
+}
+
+// Dynamic shared memory of a kernel, and the blocks of it that fit on the
+// current device at once, set and measured once per device.
+template <typename K>
+inline cudaError_t kernel_setup(DeviceOnce& o, K kern, int threads, size_t smem, int* resident) {
+  return device_once(o, resident, [&](int dev, int* v) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int sms = 0, per_sm = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    *v = sms * per_sm;
+    return e;
+  });
+}
 
 // ---------------------------------------------------------------- complex
 

@@ -196,19 +196,12 @@ __global__ void k_schedule(const TmplMeta* __restrict__ meta, int n_t, int* cnt,
 template <int SRC, int TAPS>
 cudaError_t launch_persist_t(const PersistArgs& p, cudaStream_t s, size_t smem) {
   auto kern = k_persist<SRC, TAPS>;
-  static int attr_done = 0;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_done = 1;
-  }
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPT, smem);
+  static DeviceOnce once;
+  int resident = 0;
+  const cudaError_t e = kernel_setup(once, kern, kPT, smem, &resident);
   if (e != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  kern<<<sms * per_sm, kPT, smem, s>>>(p);
+  if (resident < 1) return cudaErrorInvalidConfiguration;
+  kern<<<resident, kPT, smem, s>>>(p);
   return cudaGetLastError();
 }
 

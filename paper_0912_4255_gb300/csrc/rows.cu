@@ -21,22 +21,12 @@ cudaError_t FS_CAT(rows, FS_REAL, FS_L2)(const RowsArgs<FS_REAL>& a, dim3 grid, 
   constexpr int NT = threads_for<R>(L2, 2 * RR);
   constexpr size_t SM = rows_smem<R, L2, RR>();
   auto kern = a.band ? k_rows<R, L2, RR, NT, true> : k_rows<R, L2, RR, NT, false>;
-  static int attr_done[2] = {0, 0};
-  if (!attr_done[a.band ? 1 : 0]) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM);
-    if (e != cudaSuccess) return e;
-    attr_done[a.band ? 1 : 0] = 1;
-  }
   // persistent grid: the blocks that fit on the device at once
-  static int resident = 0;
-  if (!resident) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, SM);
-    if (e != cudaSuccess) return e;
-    resident = sms * (per_sm > 0 ? per_sm : 1);
-  }
+  static DeviceOnce once[2];
+  int resident = 0;
+  const cudaError_t e = kernel_setup(once[a.band ? 1 : 0], kern, NT, SM, &resident);
+  if (e != cudaSuccess) return e;
+  if (resident < 1) resident = 1;
   const unsigned total = grid.x * grid.y;
   kern<<<total < (unsigned)resident ? total : (unsigned)resident, NT, SM, s>>>(a);
   return cudaGetLastError();
