@@ -8,7 +8,7 @@
   around 20 injections; the adjoint gradient of a sample of candidates
   against the oracle's central differences, then 50 preconditioned ascent
   steps for all 512.
-The measured numbers are appended to gpurun-style JSON lines in the file
+The measured numbers are appended as JSON lines to the file
 named by the FSTAT_RESULTS environment variable, if set."""
 import json
 import os
