@@ -20,6 +20,11 @@ data", LIGO-P0900301):
                 direct demodulation (Eqs. 7-8) at arbitrary frequencies, the
                 single-bin form and its finite-difference gradient.
 * ``inject``    signal injection (Eqs. 1-4) and the optimal SNR rho^2.
+* ``candidates`` per-band top-k of 2F rows (the plain definition).
+* ``frontend``  the SFT front end of Sec. III.B (normalisation, Dirichlet
+                merge of Eq. e9, band selection, inverse transform, stitching).
+* ``demod``     the SFT-domain demodulation F-statistic of the speed
+                comparison (Sec. IV.A), from Eq. 7 and Eq. e9's kernel.
 
 Parity status of each function is stated in its docstring; every function is
 pinned by a ``-m "not gpu"`` test except where the docstring says
