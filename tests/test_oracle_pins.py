@@ -75,6 +75,30 @@ def test_antenna_functions_follow_eqs_2_3(seed):
         assert np.max(np.abs(fx - (b * c - a * s))) < 1e-12
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_sky_average_of_beam_power_is_two_fifths(seed):
+    """Eqs. 2-3 give F_+^2 + F_x^2 = a^2 + b^2 (zeta = 90 deg) at every
+    polarisation angle, and the average of F_+^2 + F_x^2 of an interferometer
+    with perpendicular arms over an isotropic sky is the textbook 2/5, for
+    any latitude and arm orientation.  A wrong coefficient in the closed form
+    of a, b (one that the orthogonal-map pin above cannot see, e.g. a common
+    scale) breaks it.  The sky and one sidereal day are sampled exactly for
+    the harmonics involved."""
+    g = synth.rng(40 + seed)
+    det = synth.Detector(lat_rad=g.uniform(-1.4, 1.4), lon_rad=g.uniform(-3, 3),
+                         gamma_rad=g.uniform(0, math.pi))
+    plan = synth.PlanDesc(det=det)
+    alpha, delta = synth.fibonacci_sky(4096)
+    t = np.linspace(0.0, plan.eph.sidereal_day_s, 16, endpoint=False)
+    tot = cross = 0.0
+    for al, de in zip(alpha, delta):
+        a, b = G.beam_ab(t, al, de, plan.det, plan.eph)[:2]
+        tot += np.mean(a * a + b * b)
+        cross += np.mean(a * b)
+    assert abs(tot / len(alpha) - 0.4) < 1e-5
+    assert abs(cross / len(alpha)) < 1e-6
+
+
 def test_beam_zenith_unit_response():
     """Sec. II after Eq. 3 (zeta = 90 deg): for a source at the zenith the
     response to an optimally oriented wave is 1, i.e. a^2 + b^2 = 1."""
