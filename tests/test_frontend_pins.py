@@ -158,3 +158,67 @@ def test_normalised_noise_has_the_window_mean_square():
     x = FE.sft_to_series(X, np.arange(M) * T_SFT, d, 0.0, M * N1)
     want = np.mean(FE.tukey(M * N1, 0.2) ** 2)
     assert abs(np.mean(np.abs(x) ** 2) / want - 1) < 0.1
+
+
+def test_tukey_window_closed_forms():
+    """Sec. III.B.5's band window, pinned by what defines a Tukey window
+    rather than by re-evaluating its formula.  Sampled at x = (i + 1/2)/n
+    with taper width e = frac/2 of the band on each side:
+    * it is 1 on the flat part e <= x <= 1 - e and symmetric, w[i] = w[n-1-i];
+    * it is 1/2 at the middle of each taper (x = e/2, which is a sample here);
+    * on the rise it is the half-angle form sin^2(pi x / (2 e)), so samples
+      at x and e - x add up to 1;
+    * its mean is 1 - frac/2 exactly when n e is a whole number (the cosine
+      part sums to zero over the midpoint samples of a half period);
+    * frac = 1 is the Hann window sin^2(pi x); frac = 0 is all ones.
+    A grid x = i/n, e = frac instead of frac/2, a flipped cosine sign or a
+    missing mirrored fall each break at least one of these."""
+    n, frac = 20, 0.3                       # e = 0.15 = 3 samples, x = e/2 at i = 1
+    w = FE.tukey(n, frac)
+    x = (np.arange(n) + 0.5) / n
+    e = frac / 2
+    assert np.allclose(w, w[::-1], atol=1e-15, rtol=0)
+    assert np.all(w[(x >= e) & (x <= 1 - e)] == 1.0)
+    assert abs(w[1] - 0.5) < 1e-15 and abs(w[n - 2] - 0.5) < 1e-15
+    rise = x < e
+    assert np.allclose(w[rise], np.sin(math.pi * x[rise] / (2 * e)) ** 2, atol=1e-15, rtol=0)
+    assert abs(w[0] + w[2] - 1.0) < 1e-15
+    assert np.all(np.diff(w[:4]) > 0) and 0 < w[0] < 0.5
+    assert abs(w.mean() - (1 - frac / 2)) < 1e-15
+    for n2, f2 in ((64, 0.25), (1000, 0.1), (36, 1.0 / 3.0)):
+        assert abs(FE.tukey(n2, f2).mean() - (1 - f2 / 2)) < 1e-13
+    xh = (np.arange(64) + 0.5) / 64
+    assert np.allclose(FE.tukey(64, 1.0), np.sin(math.pi * xh) ** 2, atol=1e-15, rtol=0)
+    assert np.all(FE.tukey(64, 0.0) == 1.0)
+
+
+@pytest.mark.parametrize("taper", [5, 16])
+def test_edge_taper_of_a_constant_chunk(taper):
+    """Sec. III.B.6 (chunk stitching, optional taper at the chunk ends): a
+    sinusoid at exactly the heterodyne frequency makes every chunk of x_h a
+    constant (one SFT bin, Eq. e9 exact, Tukey window 1 at the band centre).
+    With the taper, the first and last e samples of each chunk are that
+    constant times the raised cosine sin^2(pi (i + 1/2) / (2 e)), i = 0..e-1
+    at the start and mirrored at the end; the rest of the chunk and the gap
+    are untouched.  The taper of e samples sums to e/2, and its samples i
+    and e-1-i add up to 1.  A taper that starts at i instead of i + 1/2, a
+    flipped cosine, or a missing or unmirrored end taper fails."""
+    d = _desc()
+    slots = np.array([0, 1, 2, 5, 6, 7])                 # two chunks of 3 SFTs
+    x_raw = synth.raw_sinusoids(8 * N, DT, [K_H / T_SFT], [1.5], [0.4])
+    X = synth.sfts_of(x_raw, slots, N, d.k_lo, d.n_bins, dtype=np.complex128)
+    n_out = 8 * N1
+    flat = FE.sft_to_series(X, slots * T_SFT, d, 0.0, n_out)
+    tap = FE.sft_to_series(X, slots * T_SFT, d.replace(edge_taper=taper), 0.0, n_out)
+    i = np.arange(taper)
+    r = np.sin(math.pi * (i + 0.5) / (2 * taper)) ** 2
+    assert abs(r.sum() - taper / 2) < 1e-12 and np.allclose(r + r[::-1], 1.0, atol=1e-15)
+    for a, m in ((0, 3), (5, 3)):
+        lo, hi = a * N1, (a + m) * N1
+        c = flat[lo:hi]
+        assert np.abs(c - c[0]).max() < 1e-9 * abs(c[0])      # the chunk is one constant
+        ratio = tap[lo:hi] / c
+        assert np.abs(ratio[:taper] - r).max() < 1e-12
+        assert np.abs(ratio[-taper:] - r[::-1]).max() < 1e-12
+        assert np.abs(ratio[taper:-taper] - 1.0).max() < 1e-12
+    assert np.all(tap[3 * N1:5 * N1] == 0) and np.all(flat[3 * N1:5 * N1] == 0)

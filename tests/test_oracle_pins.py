@@ -425,6 +425,32 @@ def test_single_bin_form_matches_fft_bin():
         assert abs(F.single_bin_two_f(x, tm, NOGAPS, plan, fr[q]) - r[q]) < 1e-9 * max(r[q], 1)
 
 
+def test_single_bin_many_matches_single_bin_and_fft_bins():
+    """``single_bin_two_f_many`` (the sampled-bin reference of the full-size
+    parity tests) is ``single_bin_two_f`` evaluated at several offsets: equal
+    to it at off-grid frequencies, and equal to the FFT path (itself pinned
+    by brute-force DFT) at bin frequencies.  A wrong sign or scale of the
+    frequency fails (a shift of the phase reference does not change 2F)."""
+    plan = small_plan(n_data=3000, n_fft=4096, interp=R.SINC)
+    x = synth.complex_noise(plan.n_data, 1.0, 19)
+    inj = synth.random_injection(23, df=0.27, fdot=-2e-9)
+    x = x + I.inject(np.zeros(plan.n_data, np.complex128), [inj], plan,
+                     np.ones(plan.n_data, bool))[0]
+    tm = synth.make_templates(inj.alpha, inj.delta, inj.fdot, 0, plan.n_data)[0]
+    r = F.resample_two_f(x, tm, NOGAPS, plan)
+    fr = F.bin_frequencies(plan.n_fft, plan.dt)
+    qs = [0, 17, 2048, int(np.argmax(r)), 3001, 4095]
+    many = F.single_bin_two_f_many(x, tm, NOGAPS, plan, fr[qs])
+    for q, v in zip(qs, many):
+        assert abs(v - r[q]) < 1e-9 * max(r[q], 1)
+    offs = [0.27, -0.3112, 0.0001, 0.9]
+    many = F.single_bin_two_f_many(x, tm, NOGAPS, plan, offs)
+    for f, v in zip(offs, many):
+        one = F.single_bin_two_f(x, tm, NOGAPS, plan, f)
+        assert abs(v - one) < 1e-12 * max(one, 1)
+    assert many[0] > 50 * np.median(r)                 # the injection is where it belongs
+
+
 def test_gradient_analytic_in_f_and_fdot():
     """d2F/df and d2F/dfdot have closed forms from dF_a/df = sum w_a
     (-2 pi i tau) e and dw/dfdot = -i pi tau^2 w; the finite-difference
