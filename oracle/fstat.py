@@ -71,7 +71,10 @@ def resampled_series(x_h, tmpl, gaps, plan):
                                    int(tmpl["span_len"]), gaps)
     m = resample.mask(u, valid)
     z = resample.interpolate(x_h, u, valid, plan.interp, plan.taps, plan.window)
-    tau = tb - T                                       # t_m(T^k), Eq. phi-s-explain
+    # t_m(T^k) of Eq. phi-s-explain, evaluated at T^k: equal to t_b^k - T^k
+    # by Eq. 21, but the difference of the two absolute times carries the
+    # rounding of T (1 ulp = 4.7e-10 s at 30 d, 3e-6 rad at f_h = 1 kHz)
+    tau = geometry.roemer_delay(T, a_, d_, plan.det, plan.eph)
     tau_b = tb - plan.t_start
     # phase in cycles, reduced mod 1 before the complex exponential
     cyc = _frac(plan.f_het * tau) + _frac(0.5 * fdot * tau_b * tau_b) + _frac(fddot * tau_b ** 3 / 6.0)
