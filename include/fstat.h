@@ -270,11 +270,16 @@ int fstat_debug_stall(fstat_plan_t p, int64_t template_index);
  * synchronisation of cudaMalloc/cudaFree.  It takes the plan descriptor
  * directly (no plan, no workspace) and computes exactly what fstat_compute
  * computes, template by template, using only a fixed scratch array of about
- * 17 MiB that the library reserves in device memory when it is loaded (on
- * every GPU that loads it, until the process exits).  It calls no
- * cudaMalloc, cudaFree or other allocating routine.
+ * 17 MiB in device memory, part of the library's device code: a GPU
+ * reserves it when that code is loaded on it (with CUDA's default lazy
+ * loading, at this entry point's first call there) and holds it until the
+ * process exits.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.  The descriptor is validated as fstat_plan validates it (same
+ * codes; max_templates is not used), then:
  * Limits: n_fft <= 2^20 (else FSTAT_ERANGE); precision MIXED or FP32 (FP64
- * gives FSTAT_ENOTSUP); taps <= 16.
+ * gives FSTAT_ENOTSUP); taps <= 16.  It runs on the current device, and
+ * x_h, templates, gaps and twoF must be that device's memory (FSTAT_EINVAL
+ * otherwise); twoF holds n_t * n_fft floats.
  * The first call on a device looks up the array's device address with that
  * device current, fills its twiddle tables and synchronises the stream; make
  * that first call before any stream capture.  All calls on a device share
@@ -285,6 +290,33 @@ int fstat_debug_stall(fstat_plan_t p, int64_t template_index);
 int fstat_compute_noalloc(const fstat_plan_desc *d, const float *x_h, const fstat_template *templates,
                           int64_t n_t, const int64_t *gaps, int64_t n_gaps_total, float *twoF,
                           void *stream);
+
+/* Self-test of the single-precision device math written out by hand in the
+ * resampler (step 4 of Sec. III.A.2: the windowed-sinc weights; Eq. absorb
+ * and Eq. phi-s-explain: the phase rotation exp(-2 pi i r)), evaluated on
+ * the GPU so that tests can bound it against exact values and against
+ * CUDA's own sincospif.  For each of the n inputs in[i] (device, float32)
+ * it writes two floats out[2i], out[2i+1] (device, 8-byte aligned):
+ *   FSTAT_SELFTEST_SINCOSPI_SMALL  sin(pi x), cos(pi x) by the truncated
+ *                                  Taylor series used for |x| <= 1/4;
+ *   FSTAT_SELFTEST_SINCOSPIF       the same from CUDA's sincospif;
+ *   FSTAT_SELFTEST_EXPM2PI         Re, Im of exp(-2 pi i r), |r| <= 1/2;
+ *   FSTAT_SELFTEST_SINC8_LANCZOS / _RECT  the 8-tap windowed-sinc
+ *      interpolant (Lanczos window or plain truncation) of the complex64
+ *      run aux[0 .. n_aux) at the fractional index u = in[i]; taps outside
+ *      the run weigh zero, u outside [0, n_aux) gives NaN.
+ * aux is used only by the interpolation tests (device, 8-byte aligned,
+ * 8 <= n_aux <= 2^22).  Errors: EINVAL (unknown test, null or misaligned
+ * pointer), ERANGE (n > 2^30), ECUDA.  Asynchronous on stream; no plan. */
+enum {
+  FSTAT_SELFTEST_SINCOSPI_SMALL = 0,
+  FSTAT_SELFTEST_SINCOSPIF = 1,
+  FSTAT_SELFTEST_EXPM2PI = 2,
+  FSTAT_SELFTEST_SINC8_LANCZOS = 3,
+  FSTAT_SELFTEST_SINC8_RECT = 4
+};
+int fstat_selftest_math(int which, const float *in, int64_t n, const float *aux, int64_t n_aux, float *out,
+                        void *stream);
 
 /* Per-band top-k candidates of 2F spectra.  The paper computes 2F in every
  * frequency bin (Eq. 6, step 7 of Sec. III.A.2) for searches over many

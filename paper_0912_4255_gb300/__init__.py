@@ -26,7 +26,7 @@ __all__ = [
     "fstat_status", "fstat_destroy", "fstat_strerror", "fstat_template_nb", "pack_templates",
     "fstat_profile", "fstat_profile_read", "KERNEL_KINDS", "GraphRunner", "fstat_debug_stall", "fstat_topk",
     "fstat_inject", "pack_injections", "INJECTION_DTYPE", "fstat_sft_series", "fstat_sft_workspace",
-    "fstat_sft_normalize", "fstat_sft_demod",
+    "fstat_sft_normalize", "fstat_sft_demod", "fstat_selftest_math",
     "NEAREST", "SINC", "WIN_RECT", "WIN_LANCZOS", "PREC_MIXED", "PREC_FP64", "PREC_FP32",
     "MODE_FUSED", "MODE_PLAIN", "MODE_PERSISTENT", "MODE_SPLIT", "TEMPLATE_DTYPE",
 ]
@@ -210,16 +210,44 @@ def fstat_compute(plan: Plan, x_h, templates, gaps=None, twoF=None, stream=None)
 def fstat_compute_noalloc(desc, x_h, templates, gaps=None, twoF=None, stream=None):
     """fstat_compute without a plan or workspace: the library uses its own
     fixed scratch array (n_fft <= 2^20), for callers that cannot allocate
-    device memory.  ``twoF`` should be passed in by such callers."""
+    device memory.  ``twoF`` (float32, at least n_templates * n_fft values)
+    should be passed in by such callers.  The call runs on x_h's device, on
+    that device's current stream unless ``stream`` is given; every tensor
+    must live on that device."""
     import torch
+    assert x_h.is_cuda and x_h.dtype == torch.complex64 and x_h.is_contiguous()
+    dev = x_h.device
     lib = _lib.load()
     n_t = _n_templates(templates)
-    if twoF is None:
-        twoF = torch.empty(n_t * int(desc.n_fft), dtype=torch.float32, device=x_h.device)
-    g, ng = _gap_args(gaps)
-    _check(lib.fstat_compute_noalloc(ctypes.byref(_desc(desc)), _ptr(x_h), _ptr(templates), n_t, g, ng,
-                                     _ptr(twoF), _stream(stream)), "fstat_compute_noalloc")
+    need = n_t * int(desc.n_fft)
+    for name, t in (("templates", templates), ("gaps", gaps), ("twoF", twoF)):
+        if t is not None and t.device != dev:
+            raise ValueError(f"fstat_compute_noalloc: {name} is on {t.device}, x_h on {dev}")
+    if twoF is not None and (twoF.dtype != torch.float32 or not twoF.is_contiguous() or twoF.numel() < need):
+        raise ValueError(f"fstat_compute_noalloc: twoF must be contiguous float32 with >= {need} values")
+    with torch.cuda.device(dev):
+        if twoF is None:
+            twoF = torch.empty(need, dtype=torch.float32, device=dev)
+        g, ng = _gap_args(gaps)
+        s = _stream(torch.cuda.current_stream(dev) if stream is None else stream)
+        _check(lib.fstat_compute_noalloc(ctypes.byref(_desc(desc)), _ptr(x_h), _ptr(templates), n_t, g, ng,
+                                         _ptr(twoF), s), "fstat_compute_noalloc")
     return twoF
+
+
+SELFTEST = {"sincospi_small": 0, "sincospif": 1, "expm2pi": 2, "sinc8_lanczos": 3, "sinc8_rect": 4}
+
+
+def fstat_selftest_math(which: str, x, aux=None, stream=None):
+    """The device math of the resampler on inputs x (float32, CUDA):
+    a [n, 2] float32 tensor (fstat_selftest_math of the C ABI)."""
+    import torch
+    assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()
+    out = torch.empty((x.numel(), 2), dtype=torch.float32, device=x.device)
+    n_aux = 0 if aux is None else aux.numel()
+    _check(_lib.load().fstat_selftest_math(SELFTEST[which], _ptr(x), x.numel(), _ptr(aux), n_aux, _ptr(out),
+                                           _stream(stream)), "fstat_selftest_math")
+    return out
 
 
 def fstat_resample(plan: Plan, x_h, templates, gaps=None, stream=None):

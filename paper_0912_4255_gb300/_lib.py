@@ -92,6 +92,8 @@ SYMBOLS = {
     "fstat_compute_noalloc": (ctypes.c_int, [ctypes.POINTER(PlanDesc), c_void_p, c_void_p, c_int64,
                                              c_void_p, c_int64, c_void_p, c_void_p]),
     "fstat_debug_stall": (ctypes.c_int, [c_void_p, c_int64]),
+    "fstat_selftest_math": (ctypes.c_int, [ctypes.c_int, c_void_p, c_int64, c_void_p, c_int64, c_void_p,
+                                           c_void_p]),
     "fstat_topk": (ctypes.c_int, [c_void_p, c_int64, c_int64, c_int64, ctypes.c_int, c_void_p, c_void_p,
                                   c_void_p]),
     "fstat_set_band": (ctypes.c_int, [c_void_p, c_int64, c_int64]),

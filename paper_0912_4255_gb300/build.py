@@ -38,7 +38,8 @@ def units():
            ("grad", "grad.cu", []), ("persist", "persist.cu", []),
            ("noalloc", "noalloc.cu", []), ("topk", "topk.cu", []),
            ("inject", "inject.cu", []), ("frontend", "frontend.cu", []),
-           ("demod", "demod.cu", [])]
+           ("demod", "demod.cu", []),
+           ("selftest", "selftest.cu", [])]
     for real in ("float", "double"):
         for L in LOGS:
             out.append((f"cols_{real}_{L}", "cols.cu", [f"-DFS_REAL={real}", f"-DFS_L1={L}"]))

@@ -134,10 +134,15 @@ Chunk chunk_at(fstat_plan_s* p, const fstat_template* t, int nt) {
 }
 
 
-int check_desc(const fstat_plan_desc* d) {
+}  // namespace
+
+// Host-side validation of a plan descriptor (shared with the allocation-free
+// entry point, which takes a descriptor without a plan).
+int fs::check_plan_desc(const fstat_plan_desc* d) {
   if (!d) return FSTAT_EINVAL;
-  if (!(finite(d->dt) && d->dt > 0) || !finite(d->t_start) || !(finite(d->sigma2) && d->sigma2 > 0) ||
-      !finite(d->f_het) || d->n_data < 2 || d->max_templates < 1)
+  auto fin_ = [](double v) { return isfinite(v) != 0; };
+  if (!(fin_(d->dt) && d->dt > 0) || !fin_(d->t_start) || !(fin_(d->sigma2) && d->sigma2 > 0) ||
+      !fin_(d->f_het) || d->n_data < 2 || d->max_templates < 1)
     return FSTAT_EINVAL;
   if (d->interp != FSTAT_NEAREST && d->interp != FSTAT_SINC) return FSTAT_EINVAL;
   if (d->window != FSTAT_WIN_RECT && d->window != FSTAT_WIN_LANCZOS) return FSTAT_EINVAL;
@@ -151,11 +156,13 @@ int check_desc(const fstat_plan_desc* d) {
                         d->eph.au_m, d->eph.year_s, d->eph.sidereal_day_s, d->eph.obliquity_rad,
                         d->eph.orb_phase0, d->eph.sid_phase0};
   for (double v : geo)
-    if (!finite(v)) return FSTAT_EINVAL;
+    if (!fin_(v)) return FSTAT_EINVAL;
   if (!(d->eph.year_s > 0) || !(d->eph.sidereal_day_s > 0) || d->det.radius_m < 0 || d->eph.au_m < 0)
     return FSTAT_EINVAL;
   return FSTAT_OK;
 }
+
+namespace {
 
 // twiddle tables and window constants, built in FP64 on the host
 int build_tables(fstat_plan_s* p) {
@@ -280,7 +287,7 @@ const char* fstat_strerror(int code) {
 int fstat_plan(fstat_plan_t* out, const fstat_plan_desc* d, size_t* workspace_bytes) {
   if (!out) return FSTAT_EINVAL;
   *out = nullptr;
-  int rc = check_desc(d);
+  int rc = check_plan_desc(d);
   if (rc) return rc;
   fstat_plan_s* p = new (std::nothrow) fstat_plan_s();
   if (!p) return FSTAT_ENOMEM;

@@ -1035,6 +1035,10 @@ inline void derive_constants(PlanConst& pc) {
   pc.inv_dt = 1.0 / pc.dt;
 }
 
+// Host-side validation of a plan descriptor: FSTAT_OK or the error code
+// fstat_plan returns for it (api.cu).
+int check_plan_desc(const fstat_plan_desc* d);
+
 // Host copy of the t_b-grid computation (same formulas, FP64) used to size
 // work and by fstat_template_nb.
 int64_t host_nb(const PlanConst& pc, const fstat_template& t, double* tb0);

@@ -9,8 +9,11 @@
 // workspace it allocated.
 //
 // Instead, every piece of scratch this path uses lives in one file-scope
-// static __device__ array of fixed size, reserved when the library is
-// loaded and held by every GPU that loads it until the process exits:
+// static __device__ array of fixed size.  A device reserves it when the
+// library's device code is loaded there, which under CUDA's default lazy
+// loading is the first call of this entry point on that device (its
+// cudaGetSymbolAddress); from then on the device holds it until the process
+// exits.  It holds:
 // the FFT intermediate of one template, its knot records, block partial
 // sums, counters, the twiddle tables and the window constants.  Templates
 // are processed one after another through that single scratch area.
@@ -24,6 +27,9 @@
 // and window tables with a kernel, and synchronises the caller's stream; it
 // should therefore come before any stream capture.  Later calls only
 // enqueue work.
+//
+// Device: the call runs on the current device; x_h, the templates, the
+// gaps and twoF must be memory of that device (FSTAT_EINVAL otherwise).
 //
 // Sharing: every call on a device uses the same array and leaves its last
 // contents there.  Counters are cleared at the start of each template;
@@ -132,7 +138,18 @@ int setup_device(cudaStream_t s, char** base_out) {
   return FSTAT_OK;
 }
 
-bool fin(double v) { return isfinite(v) != 0; }
+// A device pointer that the current device can use: memory of this device
+// (or managed memory).  Host memory and another GPU's memory are refused
+// before anything is launched.
+bool on_current_device(const void* p, int dev) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
 
 }  // namespace
 
@@ -146,22 +163,25 @@ extern "C" int fstat_compute_noalloc(const fstat_plan_desc* d, const float* x_h,
   if (!d || !x_h || (n_t > 0 && (!templates || !twoF)) || n_t < 0) return FSTAT_EINVAL;
   if (((uintptr_t)x_h & 7) || ((uintptr_t)templates & 7) || ((uintptr_t)twoF & 3)) return FSTAT_EINVAL;
   if (n_gaps_total < 0 || (n_gaps_total > 0 && (!gaps || ((uintptr_t)gaps & 7)))) return FSTAT_EINVAL;
-  if (!(fin(d->dt) && d->dt > 0) || !fin(d->t_start) || !(fin(d->sigma2) && d->sigma2 > 0) || !fin(d->f_het) ||
-      d->n_data < 2 || d->n_data > ((int64_t)1 << 30))
-    return FSTAT_EINVAL;
-  if (d->interp != FSTAT_NEAREST && d->interp != FSTAT_SINC) return FSTAT_EINVAL;
-  if (d->window != FSTAT_WIN_RECT && d->window != FSTAT_WIN_LANCZOS) return FSTAT_EINVAL;
+  // the descriptor is checked as fstat_plan checks it (max_templates plays
+  // no part here), then against the limits of the scratch array
+  fstat_plan_desc dd = *d;
+  if (dd.max_templates < 1) dd.max_templates = 1;
+  int rc = check_plan_desc(&dd);
+  if (rc) return rc;
   if (d->precision == FSTAT_PREC_FP64) return FSTAT_ENOTSUP;
-  if (d->precision != FSTAT_PREC_MIXED && d->precision != FSTAT_PREC_FP32) return FSTAT_EINVAL;
-  if (d->interp == FSTAT_SINC && (d->taps < 2 || d->taps > 2 * kNaMaxHalf || (d->taps & 1))) return FSTAT_ENOTSUP;
-  if (d->n_fft < ((int64_t)1 << kMinLog) || d->n_fft > kNaMaxN || (d->n_fft & (d->n_fft - 1)))
-    return FSTAT_ERANGE;   // the scratch array holds one FFT of at most 2^20 points
-  if (fabs(d->f_het * d->dt) > 1e6 || !(d->eph.year_s > 0) || !(d->eph.sidereal_day_s > 0)) return FSTAT_ERANGE;
+  if (d->interp == FSTAT_SINC && d->taps > 2 * kNaMaxHalf) return FSTAT_ENOTSUP;
+  if (d->n_fft > kNaMaxN) return FSTAT_ERANGE;   // the scratch array holds one FFT of at most 2^20 points
   if (n_t == 0) return FSTAT_OK;
 
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return FSTAT_ECUDA;
+  if (!on_current_device(x_h, dev) || !on_current_device(templates, dev) || !on_current_device(twoF, dev) ||
+      (n_gaps_total > 0 && !on_current_device(gaps, dev)))
+    return FSTAT_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   char* base = nullptr;
-  int rc = setup_device(s, &base);
+  rc = setup_device(s, &base);
   if (rc) return rc;
 
   PlanConst pc;
@@ -186,7 +206,7 @@ extern "C" int fstat_compute_noalloc(const fstat_plan_desc* d, const float* x_h,
   if (sh.l2 < 6 || sh.l2 > 12) return FSTAT_ENOTSUP;
   sh.cols = cols_per_block(pc.precision, sh.l1);
   sh.rows = rows_per_block(pc.precision, sh.l2);
-  if (sh.cols <= 0 || sh.rows <= 0) return FSTAT_ENOTSUP;
+  if (sh.cols <= 0 || sh.rows <= 0 || sh.cols > (1 << sh.l2) || sh.rows > (1 << sh.l1)) return FSTAT_ENOTSUP;
 
   // twiddle table pointers inside the scratch array
   Tw<float> twf;

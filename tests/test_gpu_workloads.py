@@ -47,9 +47,9 @@ def test_precision_stress_all_modes():
         errs[name] = (float(np.max(rel)), float(np.median(rel)), float(got[0][q_inj] / info[0][1]))
     _record("precision_stress", rho2=info[0][1], oracle_peak=float(ref[q_inj]),
             **{k: {"max_rel": v[0], "median_rel": v[1], "peak_over_rho2": v[2]} for k, v in errs.items()})
-    # FP64 evaluation: the floor is the cubic interpolation of a, b between
-    # knots (~1e-7) and the float32 output; mixed: the parity tolerance
-    assert errs["fp64"][0] <= 1e-5
+    # FP64 evaluation: measured 4.2e-7 max and 2.6e-8 median (the median is
+    # the rounding of the float32 output); mixed: the parity tolerance
+    assert errs["fp64"][0] <= 1e-6
     assert errs["mixed"][0] <= 1e-4
     # all-FP32 time map: the phase f_h t_m ~ 5e5 cycles cannot be held in FP32
     assert errs["fp32"][0] > 1e-2
