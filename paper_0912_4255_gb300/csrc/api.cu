@@ -52,8 +52,6 @@ struct fstat_plan_s {
 
 namespace {
 
-bool finite(double v) { return isfinite(v) != 0; }
-
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 int ilog2(int64_t n) {
