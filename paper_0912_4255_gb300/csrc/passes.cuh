@@ -239,8 +239,20 @@ __device__ __forceinline__ void cols_tile(const ColsArgs<R>& a, int t, int tile,
     Cx x[RADL];
 #pragma unroll
     for (int q = 0; q < RADL; ++q) x[q] = buf[f * STRIDE + pidx(j + q * NS)];
+    {
+      // the stage twiddles W^(q j): the powers q = 1, 2, 4, 8 from the table,
+      // the others as products of at most three of them (shared-memory
+      // bandwidth, not arithmetic, limits this pass)
+      Cx wp[RADL];
+      wp[1] = tlast[j];
 #pragma unroll
-    for (int q = 1; q < RADL; ++q) x[q] = cmul(x[q], tlast[(q - 1) * NS + j]);
+      for (int q = 2; q < RADL; ++q) {
+        if ((q & (q - 1)) == 0) wp[q] = tlast[(q - 1) * NS + j];
+        else { const int hb = (q & 8) ? 8 : ((q & 4) ? 4 : 2); wp[q] = cmul(wp[hb], wp[q - hb]); }
+      }
+#pragma unroll
+      for (int q = 1; q < RADL; ++q) x[q] = cmul(x[q], wp[q]);
+    }
     Dft<Cx, RADL>::run(x);
     const int k2 = c0 + c;
     // p1 = j + q NS lands at Z[p1 / R][k2][p1 % R]; NS is a multiple of R, so
