@@ -4,13 +4,20 @@
 // band of consecutive bins, the k largest values (descending; ties: lower bin
 // first) with their bin indices.
 //
-// One block per (row, band) streams the band once with 16-byte loads.  The
-// threads' maxima of the first 2048 values give a lower bound of the band's
-// k-th largest value (k of those maxima are distinct values at least that
-// large); every value at or above the current bound is appended to a
-// shared-memory buffer, and whenever the buffer could overflow it is merged
-// with the running list by a bitonic sort, which raises the bound to the
-// list's k-th value.  In noise only a few values per band pass the bound.
+// One block per (row, band) streams the band once with 16-byte loads; every
+// thread keeps the 4 largest finite values it sees (ties: lower bin) in
+// registers.  Each warp then draws its k largest from its lanes' lists by a
+// tournament of shuffles, and one warp merges the warps' lists.  The result
+// is exact unless a thread's list was too short: when a thread's 4th value
+// is not below the band's k-th (in the order above), the thread may have
+// dropped a value of the top k, and the block redoes the band with a sweep
+// that keeps every candidate: the threads' maxima of the first 2048 values
+// give a lower bound of the band's k-th largest value (k of those maxima are
+// distinct values at least that large); every value at or above the current
+// bound is appended to a shared-memory buffer, and whenever the buffer
+// could overflow it is merged with the running list by a bitonic sort,
+// which raises the bound to the list's k-th value.  In noise a thread's 4
+// values almost never all reach the band's 16 largest.
 #include "fstat_internal.cuh"
 
 #include <climits>
@@ -77,16 +84,9 @@ __device__ float merge(float* sv, int* si, int* cnt, int k) {
   return tau;
 }
 
-__global__ void __launch_bounds__(kTopThreads)
-k_topk(const float* __restrict__ two_f, int64_t row_len, int band_len, int k, float* __restrict__ val,
-       int* __restrict__ bin) {
-  __shared__ float sv[kSortN];
-  __shared__ int si[kSortN];
-  __shared__ int cnt;
-  const int band = blockIdx.x;
-  const int64_t row = blockIdx.y;
-  const float* src = two_f + row * row_len + (int64_t)band * band_len;
-  const int base = band * band_len;
+// The sweep that keeps every candidate (all threads of the block).
+__device__ void topk_sweep(const float* __restrict__ src, int base, int64_t o, int band_len, int k,
+                           float* __restrict__ val, int* __restrict__ bin, float* sv, int* si, int& cnt) {
   // bound from the first step: the k-th largest of the threads' maxima
   float4 v4 = __ldcs(reinterpret_cast<const float4*>(src) + threadIdx.x);
   float mx = fmaxf(fmaxf(v4.x, v4.y), fmaxf(v4.z, v4.w));      // NaN only if all four are
@@ -110,7 +110,109 @@ k_topk(const float* __restrict__ two_f, int64_t row_len, int band_len, int k, fl
     // the next step adds at most kStep candidates: merge while they still fit
     if (cnt > kSortN - k - kStep || s0 + kStep >= band_len) tau = merge(sv, si, &cnt, k);
   }
+  for (int i = threadIdx.x; i < k; i += kTopThreads) {
+    val[o + i] = sv[i];
+    bin[o + i] = si[i] == INT_MAX ? -1 : si[i];
+  }
+}
+
+constexpr int kLocal = 4;                 // values kept per thread
+constexpr int kWarps = kTopThreads / 32;
+
+// The better of the warp's (v, b) pairs, in every lane.
+__device__ __forceinline__ void warp_best(float& v, int& b) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int ob = __shfl_xor_sync(0xffffffffu, b, o);
+    if (before(ov, ob, v, b)) { v = ov; b = ob; }
+  }
+}
+
+__global__ void __launch_bounds__(kTopThreads)
+k_topk(const float* __restrict__ two_f, int64_t row_len, int band_len, int k, float* __restrict__ val,
+       int* __restrict__ bin) {
+  __shared__ float sv[kSortN];
+  __shared__ int si[kSortN];
+  __shared__ int cnt;
+  __shared__ float wv[kWarps][kMaxK];
+  __shared__ int wb[kWarps][kMaxK];
+  __shared__ float kth_v;
+  __shared__ int kth_b;
+  const int band = blockIdx.x;
+  const int64_t row = blockIdx.y;
+  const float* src = two_f + row * row_len + (int64_t)band * band_len;
+  const int base = band * band_len;
   const int64_t o = (row * (row_len / band_len) + band) * k;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // this thread's 4 largest finite values, in the order of the result
+  float lv[kLocal];
+  int lb[kLocal];
+#pragma unroll
+  for (int i = 0; i < kLocal; ++i) { lv[i] = -INFINITY; lb[i] = INT_MAX; }
+  const float4* src4 = reinterpret_cast<const float4*>(src);
+#pragma unroll 4
+  for (int s0 = 0; s0 < band_len; s0 += kStep) {
+    const float4 x = __ldcs(src4 + s0 / 4 + threadIdx.x);
+    const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float v = xs[c];
+      if (v > lv[kLocal - 1] && v < INFINITY) {    // a finite value that enters the list (bins ascend)
+        const int b = base + s0 + 4 * (int)threadIdx.x + c;
+        bool placed = false;
+#pragma unroll
+        for (int i = kLocal - 1; i >= 0; --i) {
+          if (!placed) {
+            if (i > 0 && v > lv[i - 1]) { lv[i] = lv[i - 1]; lb[i] = lb[i - 1]; }
+            else { lv[i] = v; lb[i] = b; placed = true; }
+          }
+        }
+      }
+    }
+  }
+  const float last_v = lv[kLocal - 1];
+  const int last_b = lb[kLocal - 1];
+  // each warp's k largest, by rounds: the best head of the lanes' lists wins
+  // and that lane drops it
+  for (int r = 0; r < k; ++r) {
+    float v = lv[0];
+    int b = lb[0];
+    warp_best(v, b);
+    if (lane == 0) { wv[warp][r] = v; wb[warp][r] = b; }
+    if (lv[0] == v && lb[0] == b) {
+#pragma unroll
+      for (int i = 0; i < kLocal - 1; ++i) { lv[i] = lv[i + 1]; lb[i] = lb[i + 1]; }
+      lv[kLocal - 1] = -INFINITY;
+      lb[kLocal - 1] = INT_MAX;
+    }
+  }
+  __syncthreads();
+  // warp 0 merges the warps' lists (lane w holds the head of list w)
+  if (warp == 0) {
+    int p = 0;
+    for (int r = 0; r < k; ++r) {
+      float v = lane < kWarps && p < k ? wv[lane][p] : -INFINITY;
+      int b = lane < kWarps && p < k ? wb[lane][p] : INT_MAX;
+      const float hv = v;
+      const int hb = b;
+      warp_best(v, b);
+      if (lane < kWarps && p < k && hv == v && hb == b) ++p;
+      if (lane == 0) {
+        sv[r] = v;
+        si[r] = b;
+        if (r == k - 1) { kth_v = v; kth_b = b; }
+      }
+    }
+  }
+  __syncthreads();
+  // a thread whose 4th value comes before the band's k-th may have dropped
+  // one of the top k (what it dropped comes after its 4th)
+  const bool short_list = before(last_v, last_b, kth_v, kth_b);
+  if (__syncthreads_or(short_list)) {
+    topk_sweep(src, base, o, band_len, k, val, bin, sv, si, cnt);
+    return;
+  }
   for (int i = threadIdx.x; i < k; i += kTopThreads) {
     val[o + i] = sv[i];
     bin[o + i] = si[i] == INT_MAX ? -1 : si[i];

@@ -38,6 +38,23 @@ def test_topk_matches_oracle_selection(band_len, k):
     assert np.array_equal(b.astype(np.int64), ob)
 
 
+@pytest.mark.parametrize("band_len,k", [(6144, 33), (10240, 64)])
+def test_topk_bands_with_a_partial_sweep_step(band_len, k):
+    """Bands of 3 and 5 sweeps of 2048 values (not whole steps of four):
+    the last step of a band is partial.  Rows of 61440 values: noise, a
+    slowly rising ramp (many values pass the bound, the buffer fills over
+    several steps) and a row that is NaN but for a few bins."""
+    g = synth.rng(72)
+    a = g.chisquare(4, size=(3, 61440)).astype(np.float32)
+    a[1] = (np.arange(61440) % band_len).astype(np.float32) * 0.01 + g.random(61440).astype(np.float32)
+    a[2] = np.nan
+    a[2, ::5000] = 7.0
+    v, b = _gpu_topk(a, band_len, k)
+    ov, ob = CA.band_top_k(a.astype(np.float64), band_len, k)
+    assert np.array_equal(v.astype(np.float64), ov)
+    assert np.array_equal(b.astype(np.int64), ob)
+
+
 def test_topk_rising_band_merges_repeatedly():
     """A strictly increasing band: every value passes the running bound, so
     the candidate buffer fills and merges on every step."""
