@@ -7,7 +7,7 @@
 // One block per (row, band) streams the band once with 16-byte loads; every
 // thread keeps the 4 largest finite values it sees (ties: lower bin) in
 // registers.  Each warp then draws its k largest from its lanes' lists by a
-// tournament of shuffles, and one warp merges the warps' lists.  The result
+// tournament of warp reductions, and one warp merges the warps' lists.  The result
 // is exact unless a thread's list was too short: when a thread's 4th value
 // is not below the band's k-th (in the order above), the thread may have
 // dropped a value of the top k, and the block redoes the band with a sweep
@@ -119,14 +119,21 @@ __device__ void topk_sweep(const float* __restrict__ src, int base, int64_t o, i
 constexpr int kLocal = 4;                 // values kept per thread
 constexpr int kWarps = kTopThreads / 32;
 
-// The better of the warp's (v, b) pairs, in every lane.
+// An integer whose signed order is the order of the (non-NaN) float (the
+// two zeros, equal as floats, share a key).
+__device__ __forceinline__ int order_key(float v) {
+  const int i = __float_as_int(v == 0.0f ? 0.0f : v);
+  return i ^ ((i >> 31) & 0x7fffffff);
+}
+
+// The better of the warp's (v, b) pairs, in every lane: the largest value
+// by a warp reduction of its order key, then the lowest bin among the lanes
+// that hold it.
 __device__ __forceinline__ void warp_best(float& v, int& b) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float ov = __shfl_xor_sync(0xffffffffu, v, o);
-    const int ob = __shfl_xor_sync(0xffffffffu, b, o);
-    if (before(ov, ob, v, b)) { v = ov; b = ob; }
-  }
+  const int key = order_key(v);
+  const int kmax = __reduce_max_sync(0xffffffffu, key);
+  b = __reduce_min_sync(0xffffffffu, key == kmax ? b : INT_MAX);
+  v = __int_as_float(kmax ^ ((kmax >> 31) & 0x7fffffff));
 }
 
 __global__ void __launch_bounds__(kTopThreads)
