@@ -21,14 +21,19 @@ def _setup(desc, n_t=3, seed=60):
     return fs, dev, x, tm
 
 
-@pytest.mark.parametrize("mode", ["split", "fused", "persistent"])
+@pytest.mark.parametrize("mode", ["split", "fused", "persistent", "split_n2_1024"])
 def test_band_is_the_slice_of_the_full_output(mode):
     """Bit-exact: the band's values are the full output's values of the same
-    bins, every template packed at index * band length."""
+    bins, every template packed at index * band length.  split_n2_1024 runs
+    the split path with N1 = 2^7, N2 = 2^10 (the row length of the search-sized
+    FFT)."""
     desc = synth.tiny_plan(interp=synth.SINC, taps=8, max_templates=3)
     fs, dev, x, tm = _setup(desc)
     plan = fs.Plan(desc, device=dev)
-    plan.set_tuning(mode=MODES[mode])
+    if mode == "split_n2_1024":
+        plan.set_tuning(mode=MODES["split"], log2_n1=7)
+    else:
+        plan.set_tuning(mode=MODES[mode])
     td = fs.pack_templates(tm, device=dev)
     full = fs.fstat_compute(plan, x, td).cpu().numpy().reshape(3, -1)
     n = desc.n_fft
