@@ -348,6 +348,17 @@ struct GapCursor {
     while (ce <= j) { ++g; load(); }
     return j < cs;
   }
+  // the first gap that ends after j (binary search; the cursor then
+  // advances from there)
+  __device__ __forceinline__ void seek(int j) {
+    int a = 0, b = n;
+    while (a < b) {
+      const int mid = (a + b) >> 1;
+      if ((int)__ldg(gaps + 2 * mid + 1) <= j) a = mid + 1; else b = mid;
+    }
+    g = a;
+    load();
+  }
   // true iff every sample of [j0, j1] is valid; advances the cursor to j0
   __device__ __forceinline__ bool window_valid(int j0, int j1) {
     if (j0 < lo || j1 >= hi) return false;

@@ -243,6 +243,13 @@ k_resample_r8(PlanConst pc, Chunk c, int l2, int lc, const float2* __restrict__ 
   const float sc_win = lanczos ? (float)(4.0 / (3.14159265358979323846 * 3.14159265358979323846))
                                : (float)(1.0 / 3.14159265358979323846);
   GapCursor gc = make_cursor(m, gaps);
+  {
+    // start the cursor near the block's first sample: the base index of the
+    // knot interval of its first point, less a margin for the taps
+    const int b = (int)blockIdx.x * kTilesPerBlock;
+    const int kf = ((b & ((1 << (l2 - 8)) - 1)) << 8) + (((b >> (l2 - 8)) * kRunTR) << l2);
+    if (kf < n_b) gc.seek(__float_as_int(__ldg(reinterpret_cast<const float*>(kn + (kf >> pc.log2h)))) - 64);
+  }
 #pragma unroll 1
   for (int tt = 0; tt < kTilesPerBlock; ++tt) {
     const int b = (int)blockIdx.x * kTilesPerBlock + tt;
