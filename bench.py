@@ -536,7 +536,9 @@ def run_e2e_candidates(fs, plan, desc, x_np, tm, gaps_np, dev, args, world, batc
     """End to end through the public API for a search that keeps candidates:
     per step the inputs go host->device, every 2F value is computed in device
     memory, fstat_topk keeps the k loudest bins of every band, and only those
-    (values and bins) come back to pinned host memory."""
+    (values and bins) come back to pinned host memory.  The top-k of one
+    chunk runs on a second stream while the next chunk is computed (two 2F
+    buffers): its HBM streaming overlaps the compute-bound kernels."""
     import torch
     n_t = len(tm)
     n_fft = int(desc.n_fft)
@@ -545,23 +547,36 @@ def run_e2e_candidates(fs, plan, desc, x_np, tm, gaps_np, dev, args, world, batc
     g_h = torch.from_numpy(gaps_np.reshape(-1).copy()).pin_memory()
     t_h = fs.pack_templates(tm, device=None).pin_memory()
     x_d, g_d, t_d = (torch.empty_like(h, device=dev) for h in (x_h, g_h, t_h))
-    out = torch.empty(batch * n_fft, dtype=torch.float32, device=dev)
+    outs = [torch.empty(batch * n_fft, dtype=torch.float32, device=dev) for _ in range(2)]
     n_bands = n_fft // band_len
+    dv = [torch.empty((batch, n_bands, k), dtype=torch.float32, device=dev) for _ in range(2)]
+    db = [torch.empty((batch, n_bands, k), dtype=torch.int32, device=dev) for _ in range(2)]
     hv = torch.empty((n_t, n_bands, k), dtype=torch.float32).pin_memory()
     hb = torch.empty((n_t, n_bands, k), dtype=torch.int32).pin_memory()
-    cs = torch.cuda.Stream(device=dev)
+    cs = torch.cuda.Stream(device=dev)          # compute
+    ts = torch.cuda.Stream(device=dev)          # selection and result copies
+    ready = [torch.cuda.Event() for _ in range(2)]
+    freed = [torch.cuda.Event() for _ in range(2)]
+    for e in freed:
+        e.record(ts)
 
     def step():
         with torch.cuda.stream(cs):
             x_d.copy_(x_h, non_blocking=True)
             g_d.copy_(g_h, non_blocking=True)
             t_d.copy_(t_h, non_blocking=True)
-            for b0 in range(0, n_t, batch):
-                nb = min(batch, n_t - b0)
-                fs.fstat_compute(plan, x_d, t_d[b0 * tsize:(b0 + nb) * tsize], g_d, out, stream=cs)
-                v, b = fs.fstat_topk(out[:nb * n_fft], band_len, k, n_rows=nb, stream=cs)
-                hv[b0:b0 + nb].copy_(v, non_blocking=True)
-                hb[b0:b0 + nb].copy_(b, non_blocking=True)
+        for i, b0 in enumerate(range(0, n_t, batch)):
+            nb = min(batch, n_t - b0)
+            j = i & 1
+            cs.wait_event(freed[j])
+            fs.fstat_compute(plan, x_d, t_d[b0 * tsize:(b0 + nb) * tsize], g_d, outs[j], stream=cs)
+            ready[j].record(cs)
+            ts.wait_event(ready[j])
+            with torch.cuda.stream(ts):
+                fs.fstat_topk(outs[j][:nb * n_fft], band_len, k, n_rows=nb, stream=ts, val=dv[j], bins=db[j])
+                hv[b0:b0 + nb].copy_(dv[j][:nb], non_blocking=True)
+                hb[b0:b0 + nb].copy_(db[j][:nb], non_blocking=True)
+            freed[j].record(ts)
 
     step()
     torch.cuda.synchronize(dev)

@@ -366,17 +366,25 @@ def fstat_sft_demod(plan: Plan, desc, sfts, t_sft, templates, q0: int, n_q: int,
     return twoF
 
 
-def fstat_topk(two_f, band_len: int, k: int, n_rows: int | None = None, stream=None):
+def fstat_topk(two_f, band_len: int, k: int, n_rows: int | None = None, stream=None, val=None, bins=None):
     """Per-band top-k candidates of 2F rows (``two_f`` device float32 of
     n_rows x row_len, row_len = numel / n_rows): returns (values float32,
-    bins int32), each [n_rows, row_len // band_len, k], descending."""
+    bins int32), each [n_rows, row_len // band_len, k], descending, into
+    ``val`` and ``bins`` when given (contiguous, at least that size)."""
     import torch
     lib = _lib.load()
     n_rows = 1 if n_rows is None else int(n_rows)
     row_len = two_f.numel() // n_rows
     n_bands = row_len // band_len if band_len else 0
-    val = torch.empty((n_rows, n_bands, k), dtype=torch.float32, device=two_f.device)
-    bins = torch.empty((n_rows, n_bands, k), dtype=torch.int32, device=two_f.device)
+    need = n_rows * n_bands * k
+    if val is None:
+        val = torch.empty((n_rows, n_bands, k), dtype=torch.float32, device=two_f.device)
+    if bins is None:
+        bins = torch.empty((n_rows, n_bands, k), dtype=torch.int32, device=two_f.device)
+    if (val.dtype != torch.float32 or bins.dtype != torch.int32 or val.numel() < need or bins.numel() < need
+            or not val.is_contiguous() or not bins.is_contiguous()
+            or val.device != two_f.device or bins.device != two_f.device):
+        raise ValueError(f"fstat_topk: val (float32) and bins (int32) need {need} contiguous values on {two_f.device}")
     _check(lib.fstat_topk(_ptr(two_f), n_rows, row_len, int(band_len), int(k), _ptr(val), _ptr(bins),
                           _stream(stream)), "fstat_topk")
     return val, bins
