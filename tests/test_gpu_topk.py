@@ -86,3 +86,27 @@ def test_topk_after_compute_finds_the_injection():
     assert b[0, loud, 0] == ob[0, loud, 0] and ov[0, loud, 0] > 100
     chosen = ref[b[0].reshape(-1)]
     assert np.max(np.abs(v[0].reshape(-1) - chosen) / np.maximum(chosen, 4.0)) <= 1e-4
+
+
+def test_topk_into_given_tensors_on_a_second_stream():
+    """The output tensors of one call reused by the next, on a stream other
+    than the default one (as a search pipelines its chunks): the same values
+    and bins as separate calls, and wrong output tensors are refused."""
+    import torch
+    import paper_0912_4255_gb300 as fs
+    g = synth.rng(74)
+    a = torch.from_numpy(g.chisquare(4, size=(3, 16384)).astype(np.float32)).cuda()
+    want_v, want_b = fs.fstat_topk(a, 4096, 8, n_rows=3)
+    s = torch.cuda.Stream()
+    v = torch.empty((3, 4, 8), dtype=torch.float32, device="cuda")
+    b = torch.empty((3, 4, 8), dtype=torch.int32, device="cuda")
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            rv, rb = fs.fstat_topk(a, 4096, 8, n_rows=3, stream=s, val=v, bins=b)
+    s.synchronize()
+    assert rv is v and rb is b
+    assert torch.equal(v, want_v) and torch.equal(b, want_b)
+    with pytest.raises(ValueError):
+        fs.fstat_topk(a, 4096, 8, n_rows=3, val=v[:2], bins=b)
+    with pytest.raises(ValueError):
+        fs.fstat_topk(a, 4096, 8, n_rows=3, val=v, bins=b.float())
