@@ -553,8 +553,9 @@ def run_e2e_candidates(fs, plan, desc, x_np, tm, gaps_np, dev, args, world, batc
     db = [torch.empty((batch, n_bands, k), dtype=torch.int32, device=dev) for _ in range(2)]
     hv = torch.empty((n_t, n_bands, k), dtype=torch.float32).pin_memory()
     hb = torch.empty((n_t, n_bands, k), dtype=torch.int32).pin_memory()
-    cs = torch.cuda.Stream(device=dev)          # compute
-    ts = torch.cuda.Stream(device=dev)          # selection and result copies
+    # compute at the higher priority: the top-k blocks fill what it leaves
+    cs = torch.cuda.Stream(device=dev, priority=-1)         # compute
+    ts = torch.cuda.Stream(device=dev, priority=0)          # selection and result copies
     ready = [torch.cuda.Event() for _ in range(2)]
     freed = [torch.cuda.Event() for _ in range(2)]
     for e in freed:
