@@ -150,3 +150,27 @@ def test_ragged_batch_at_full_spans():
             fr = (q - n // 2) / (n * desc.dt)
             ref = F.single_bin_two_f_many(xc, tm[i], g, desc, fr)
             assert r15(row[q], ref) <= TOL, i
+
+
+@pytest.mark.parametrize("mode", ["split", "fused", "plain"])
+def test_degenerate_template_inside_a_gap(mode):
+    """A template whose whole span lies inside a gap has no valid sample:
+    A = B = C = D = 0 (Eqs. 9-10 as sums over no sample), 2F is undefined
+    and the oracle gives no finite value.  The library reports ERANGE for
+    the call, fills that template's row with NaN, and leaves the other
+    templates of the same call as the oracle has them."""
+    desc = synth.tiny_plan(interp=synth.SINC, taps=8, max_templates=3)
+    gaps = np.array([[10000, 30000]], np.int64)
+    a, dl = synth.random_sky(3, synth.SEED_BASE + 96)
+    tm = synth.make_templates(a, dl, np.zeros(3), 0, desc.n_data, 0, 1)
+    tm["span_start"][1] = 12000
+    tm["span_len"][1] = 5000                     # [12000, 17000), inside the gap
+    x, _ = injected_series(desc, synth.SEED_BASE + 97, [], gaps)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ref1 = oracle_two_f(desc, x, tm[1], gaps)
+    assert not np.any(np.isfinite(ref1))
+    got, rc = run_compute(desc, x, tm, gaps, mode=MODES[mode])
+    assert rc == -2
+    assert np.all(np.isnan(got[1]))
+    for i in (0, 2):
+        assert r15(got[i], oracle_two_f(desc, x, tm[i], gaps)) <= TOL, i

@@ -560,3 +560,26 @@ def test_band_top_k_is_a_selection():
             rest = np.delete(a[r, b * 1024:(b + 1) * 1024], bins[r, b] - b * 1024)
             assert rest.max() <= vals[r, b, -1]
     assert bins[0, 1, 0] == 1234 and vals[0, 1, 0] == 90.0
+
+
+def test_span_inside_a_gap_has_no_statistic():
+    """A template whose whole span lies inside a gap: the mask m is zero on
+    the grid (no valid source sample), so A = B = C = 0 and D = 0 (Eqs.
+    9-10 as sums over the valid samples), the weighted series are zero, and
+    2F (Eq. 6) has no finite value.  A span that overlaps the gap by part
+    keeps D > 0 and a finite 2F."""
+    desc = synth.tiny_plan(interp=synth.SINC, taps=8)
+    gaps = np.array([[10000, 30000]], np.int64)
+    x = synth.complex_noise(desc.n_data, desc.sigma2, synth.SEED_BASE + 97).astype(np.complex128)
+    tm = synth.make_templates([1.0, 1.0], [0.3, 0.3], [0.0, 0.0], 0, desc.n_data, 0, 1)
+    tm["span_start"] = [12000, 25000]
+    tm["span_len"] = [5000, 10000]              # inside the gap; half inside
+    r = F.resampled_series(x, tm[0], gaps, desc)
+    assert r["A"] == r["B"] == r["C"] == 0.0
+    assert not np.any(r["m"]) and not np.any(r["wa"]) and not np.any(r["wb"])
+    with np.errstate(divide="ignore", invalid="ignore"):
+        assert not np.any(np.isfinite(F.resample_two_f(x, tm[0], gaps, desc)))
+    r = F.resampled_series(x, tm[1], gaps, desc)
+    assert r["A"] * r["B"] - r["C"] ** 2 > 0.0
+    assert 0.4 < np.mean(r["m"]) < 0.6
+    assert np.all(np.isfinite(F.resample_two_f(x, tm[1], gaps, desc)))
