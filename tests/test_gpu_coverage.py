@@ -174,3 +174,24 @@ def test_degenerate_template_inside_a_gap(mode):
     assert np.all(np.isnan(got[1]))
     for i in (0, 2):
         assert r15(got[i], oracle_two_f(desc, x, tm[i], gaps)) <= TOL, i
+
+
+def test_sky_edges_poles_and_angle_wrap():
+    """Sky positions at the edges of their ranges: both celestial poles
+    (delta = +-pi/2, where the sidereal term of the Roemer delay vanishes),
+    the ecliptic poles, alpha at 0, 2 pi and beyond it, negative alpha;
+    2 d of data with an injection at the north pole, split mode, 8-tap
+    Lanczos.  Every bin against the oracle."""
+    d = synth.PlanDesc(dt=0.5, n_data=345600, n_fft=1 << 19, interp=R.SINC, f_het=150.0,
+                       max_templates=8)
+    inj = synth.random_injection(synth.SEED_BASE + 98, df=0.11, alpha=0.3, delta=np.pi / 2)
+    x, _ = injected_series(d, synth.SEED_BASE + 99, [inj])
+    eps = np.deg2rad(23.44)
+    al = [0.3, 0.0, 2 * np.pi, 7.0, -2.5, 3 * np.pi / 2, np.pi / 2, 1.0]
+    de = [np.pi / 2, -np.pi / 2, 0.4, -0.4, 1.1, np.pi / 2 - eps, -(np.pi / 2 - eps), 0.0]
+    tm = synth.make_templates(al, de, np.zeros(8), 0, d.n_data)
+    got, rc = run_compute(d, x, tm, mode=MODES["split"])
+    assert rc == 0
+    for i in range(len(tm)):
+        assert r15(got[i], oracle_two_f(d, x, tm[i])) <= TOL, i
+    assert np.max(got[0]) > 100                  # the injection, found at the pole
