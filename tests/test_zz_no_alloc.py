@@ -161,3 +161,28 @@ def test_noalloc_refuses_host_memory():
                                            ctypes.c_void_p(host.data_ptr()),
                                            ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == _lib.FSTAT_EINVAL
+
+
+def test_noalloc_at_its_largest_fft():
+    """n_fft = 2^20, the largest length the fixed scratch array holds (3.6 d
+    at 0.5 s, two templates, gaps): against fstat_compute and, for every bin
+    of the first template, against the oracle."""
+    import torch
+    import paper_0912_4255_gb300 as fs
+    d = synth.PlanDesc(dt=0.5, n_data=620_000, n_fft=1 << 20, f_het=120.0, max_templates=2,
+                       interp=R.SINC, taps=8)
+    gaps = synth.gap_intervals(d.n_data, 0.1, 3600, 21600, seed=15)
+    x, _ = injected_series(d, 16, [synth.random_injection(17, df=0.2)], gaps)
+    tm = synth.make_templates([0.7, 4.1], [0.2, -0.9], [0.0, -2e-9], [0, 3000], [620_000, 600_000],
+                              0, len(gaps))
+    ref, rc = run_compute(d, x, tm, gaps)
+    assert rc == 0
+    dev = torch.device("cuda:0")
+    out = torch.full((2 * d.n_fft,), float("nan"), device=dev)
+    fs.fstat_compute_noalloc(d, torch.from_numpy(x).to(dev), fs.pack_templates(tm, device=dev),
+                             torch.from_numpy(gaps.reshape(-1).copy()).to(dev), twoF=out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().reshape(2, -1)
+    for i in range(2):
+        assert r15(got[i], ref[i]) <= TOL, i
+    assert r15(got[0], oracle_two_f(d, x, tm[0], gaps)) <= TOL
