@@ -779,20 +779,15 @@ def run_montecarlo(args):
     x = raw.view(torch.complex64)
     out = torch.empty(per * desc.n_fft, dtype=torch.float32, device=dev)
     thr = (10.0, 20.0, 30.0)
-    acc = torch.zeros(5, dtype=torch.float64, device=dev)     # sum, sum of squares, tail counts
+    acc = torch.zeros(6, dtype=torch.float64, device=dev)     # count, sum, sum of squares, tail counts
     hist_edges = 40                                           # unit-width bins of 2F on [0, 40)
     hist = torch.zeros(hist_edges, dtype=torch.float64, device=dev)
     scale = math.sqrt(desc.sigma2 / 2.0)
 
     def batch():
-        torch.randn(raw.shape, generator=gen, device=dev, out=raw)
-        raw.mul_(scale)
+        raw.normal_(0.0, scale, generator=gen)
         fs.fstat_compute(plan, x, tm, None, out)
-        acc[0] += out.sum(dtype=torch.float64)
-        acc[1] += out.square().sum(dtype=torch.float64)
-        for i in range(3):
-            acc[2 + i] += (out > thr[i]).sum()
-        hist.add_(torch.histc(out, bins=hist_edges, min=0.0, max=float(hist_edges)).double())
+        fs.fstat_stats(out, acc, thr, hist, 1.0)                # one pass: moments, tails, histogram
 
     batch()                                   # warm-up (not counted)
     torch.cuda.synchronize(dev)
@@ -806,10 +801,10 @@ def run_montecarlo(args):
     torch.cuda.synchronize(dev)
     rc = fs.fstat_status(plan, raise_error=False)
     ms = ev0.elapsed_time(ev1)
-    n = float(total) * desc.n_fft
-    mean = float(acc[0]) / n
-    var = float(acc[1]) / n - mean * mean
-    tails = {f"P(2F>{int(t)})": {"measured": float(acc[2 + i]) / n,
+    n = float(acc[0])                                           # finite 2F values (all, unless a template failed)
+    mean = float(acc[1]) / n
+    var = float(acc[2]) / n - mean * mean
+    tails = {f"P(2F>{int(t)})": {"measured": float(acc[3 + i]) / n,
                                  "chi2_4": math.exp(-t / 2) * (1 + t / 2)}
              for i, t in enumerate((10.0, 20.0, 30.0))}
     # histogram against chi^2_4: P(a <= 2F < a + 1) = G(a) - G(a + 1), G(x) = e^{-x/2}(1 + x/2)
@@ -817,7 +812,8 @@ def run_montecarlo(args):
     h = hist.cpu().numpy() / n
     p_bin = np.array([sf[a] - sf[a + 1] for a in range(hist_edges)])
     sig = np.sqrt(p_bin * (1 - p_bin) / n)
-    noise_only = {"realizations": total, "two_f_values": n, "ms": ms, "two_f_values_per_s": n / (ms / 1e3),
+    noise_only = {"realizations": total, "two_f_values": float(total) * desc.n_fft, "finite_values": n, "ms": ms,
+                  "two_f_values_per_s": float(total) * desc.n_fft / (ms / 1e3),
                   "mean": mean, "var": var, "chi2_4": {"mean": 4.0, "var": 8.0}, "tails": tails,
                   "histogram": {"bins": "unit width on [0, 40)",
                                 "max_rel_dev_bins_0_20": float(np.max(np.abs(h[:20] / p_bin[:20] - 1))),
@@ -852,8 +848,7 @@ def run_montecarlo(args):
         fs.fstat_inject(plan, sig, rb, span)
         fs.fstat_compute(plan, sig, tmb, None, out)
         lam = out.view(per, -1)[:, q].double()
-        torch.randn(raw.shape, generator=gen, device=dev, out=raw)
-        raw.mul_(scale)
+        raw.normal_(0.0, scale, generator=gen)
         fs.fstat_inject(plan, x, rb, span)
         fs.fstat_compute(plan, x, tmb, None, out)
         f = out.view(per, -1)[:, q].double()

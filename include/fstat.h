@@ -334,6 +334,22 @@ int fstat_selftest_math(int which, const float *in, int64_t n, const float *aux,
 int fstat_topk(const float *twoF, int64_t n_rows, int64_t row_len, int64_t band_len, int k,
                float *val, int32_t *bin, void *stream);
 
+/* Statistics of 2F values for a Monte Carlo validation (Sec. IV.B: 2F is
+ * chi-squared with 4 degrees of freedom in Gaussian noise, non-central with a
+ * signal), in one pass over the n values of twoF.  Adds to the FP64
+ * accumulators acc[0] the number of finite values, acc[1] their sum, acc[2]
+ * the sum of their squares and acc[3 + i] the number above thr[i]
+ * (i < n_thr), and to hist[b] the number of values x >= 0 with
+ * floor(x / w) = b (the FP32 quotient, rounded once), w = bin_width,
+ * b < n_bins.  NaN and +-inf values are skipped.  twoF:
+ * device, 16-byte aligned; thr: host, n_thr <= 4 values; acc (3 + n_thr
+ * doubles) and hist (n_bins <= 256 doubles): device, added to (zero them to
+ * start).  Sums are formed in FP32 over at most 2048 values per thread,
+ * then in FP64; counts are exact.  Errors: EINVAL (bad pointers or sizes),
+ * ECUDA.  Asynchronous on stream; needs no plan. */
+int fstat_stats(const float *twoF, int64_t n, const float *thr, int n_thr, float bin_width, int n_bins,
+                double *acc, double *hist, void *stream);
+
 /* Signal injection for Monte Carlo studies (Sec. IV.B: 2F of data holding
  * a signal is non-central chi^2 with 4 degrees of freedom): adds to x_h, the
  * heterodyned complex series of the plan (complex64 [n_data], device,

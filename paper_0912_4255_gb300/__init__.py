@@ -24,7 +24,7 @@ __all__ = [
     "FstatError", "Plan", "fstat_plan", "fstat_compute", "fstat_compute_noalloc", "fstat_resample",
     "fstat_grad",
     "fstat_status", "fstat_destroy", "fstat_strerror", "fstat_template_nb", "pack_templates",
-    "fstat_profile", "fstat_profile_read", "KERNEL_KINDS", "GraphRunner", "fstat_debug_stall", "fstat_topk",
+    "fstat_profile", "fstat_profile_read", "KERNEL_KINDS", "GraphRunner", "fstat_debug_stall", "fstat_topk", "fstat_stats",
     "fstat_inject", "pack_injections", "INJECTION_DTYPE", "fstat_sft_series", "fstat_sft_workspace",
     "fstat_sft_normalize", "fstat_sft_demod", "fstat_selftest_math",
     "NEAREST", "SINC", "WIN_RECT", "WIN_LANCZOS", "PREC_MIXED", "PREC_FP64", "PREC_FP32",
@@ -388,6 +388,27 @@ def fstat_topk(two_f, band_len: int, k: int, n_rows: int | None = None, stream=N
     _check(lib.fstat_topk(_ptr(two_f), n_rows, row_len, int(band_len), int(k), _ptr(val), _ptr(bins),
                           _stream(stream)), "fstat_topk")
     return val, bins
+
+
+def fstat_stats(two_f, acc, thresholds=(), hist=None, bin_width: float = 1.0, stream=None):
+    """Adds to ``acc`` (device float64, 3 + len(thresholds) values) the count
+    of finite values of ``two_f`` (device float32), their sum, their sum of
+    squares and the counts above each threshold, and to ``hist`` (device
+    float64, one value per bin) the counts in bins of ``bin_width`` from 0,
+    in one pass."""
+    import torch
+    lib = _lib.load()
+    thr = (ctypes.c_float * max(1, len(thresholds)))(*[float(t) for t in thresholds])
+    for name, t, dt in (("acc", acc, torch.float64), ("hist", hist, torch.float64)):
+        if t is not None and (t.dtype != dt or not t.is_contiguous() or t.device != two_f.device):
+            raise ValueError(f"fstat_stats: {name} must be contiguous float64 on {two_f.device}")
+    if acc.numel() < 3 + len(thresholds):
+        raise ValueError("fstat_stats: acc needs 3 + len(thresholds) values")
+    assert two_f.is_cuda and two_f.dtype == torch.float32 and two_f.is_contiguous()
+    n_bins = 0 if hist is None else hist.numel()
+    _check(lib.fstat_stats(_ptr(two_f), two_f.numel(), thr, len(thresholds), float(bin_width), n_bins, _ptr(acc),
+                           _ptr(hist) if hist is not None else None, _stream(stream)), "fstat_stats")
+    return acc, hist
 
 
 def fstat_profile(plan: Plan, enable: bool = True):

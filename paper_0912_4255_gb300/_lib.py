@@ -96,6 +96,8 @@ SYMBOLS = {
                                            c_void_p]),
     "fstat_topk": (ctypes.c_int, [c_void_p, c_int64, c_int64, c_int64, ctypes.c_int, c_void_p, c_void_p,
                                   c_void_p]),
+    "fstat_stats": (ctypes.c_int, [c_void_p, c_int64, ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.c_float,
+                                   ctypes.c_int, c_void_p, c_void_p, c_void_p]),
     "fstat_set_band": (ctypes.c_int, [c_void_p, c_int64, c_int64]),
     "fstat_get_band": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64)]),
     "fstat_sft_workspace": (ctypes.c_size_t, [ctypes.POINTER(SftDesc), c_int64]),

@@ -39,7 +39,7 @@ def units():
            ("noalloc", "noalloc.cu", []), ("topk", "topk.cu", []),
            ("inject", "inject.cu", []), ("frontend", "frontend.cu", []),
            ("demod", "demod.cu", []),
-           ("selftest", "selftest.cu", [])]
+           ("selftest", "selftest.cu", []), ("stats", "stats.cu", [])]
     for real in ("float", "double"):
         for L in LOGS:
             out.append((f"cols_{real}_{L}", "cols.cu", [f"-DFS_REAL={real}", f"-DFS_L1={L}"]))

@@ -153,3 +153,19 @@ def test_topk_rejects_bad_arguments_on_the_host(lib):
     assert lib.fstat_topk(p, 1, 6144, 4096, 4, p, p, None) == -1             # band does not divide
     assert lib.fstat_topk(p, 70000, 4096, 2048, 4, p, p, None) == -2         # too many rows
     assert lib.fstat_topk(p, 0, 4096, 2048, 4, p, p, None) == 0              # nothing to do
+
+
+def test_stats_rejects_bad_arguments_on_the_host(lib):
+    """fstat_stats checks its sizes and pointers before any launch."""
+    import ctypes
+    p = 4096                                   # a 16-byte aligned stand-in pointer (never dereferenced)
+    thr = (ctypes.c_float * 4)(10.0, 20.0, 30.0, 40.0)
+    assert lib.fstat_stats(p, 0, thr, 3, 1.0, 40, p, p, None) == 0           # nothing to do
+    assert lib.fstat_stats(None, 8, thr, 3, 1.0, 40, p, p, None) == -1       # null input
+    assert lib.fstat_stats(p + 4, 8, thr, 3, 1.0, 40, p, p, None) == -1      # not 16-byte aligned
+    assert lib.fstat_stats(p, 8, thr, 5, 1.0, 40, p, p, None) == -1          # more than 4 thresholds
+    assert lib.fstat_stats(p, 8, thr, 3, 1.0, 257, p, p, None) == -1         # more than 256 bins
+    assert lib.fstat_stats(p, 8, thr, 3, 0.0, 40, p, p, None) == -1          # bin width 0
+    assert lib.fstat_stats(p, 8, thr, 3, 1.0, 40, p, None, None) == -1       # bins without hist
+    assert lib.fstat_stats(p, 8, thr, 3, 1.0, 40, None, p, None) == -1       # no accumulators
+    assert lib.fstat_stats(p, -1, thr, 3, 1.0, 40, p, p, None) == -1         # negative count

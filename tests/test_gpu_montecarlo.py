@@ -72,3 +72,45 @@ def test_injections_are_noncentral_chi2_4():
     assert lam.min() > 200
     assert abs(z.mean()) < 3.0 / math.sqrt(n_real), z.mean()
     assert 0.4 < z.var() < 1.8, z.var()
+
+
+def test_stats_against_numpy():
+    """fstat_stats on chi^2_4 values with NaN, +-inf and negative values
+    mixed in and a length that leaves a ragged tail: counts and histogram
+    exact, sums within FP32-partial rounding, and a second call adding
+    to the first."""
+    import torch
+    import paper_0912_4255_gb300 as fs
+    g = synth.rng(75)
+    n = 3_000_003
+    a = g.chisquare(4, size=n).astype(np.float32)
+    a[::1001] = np.nan
+    a[5::7919] = np.inf
+    a[7::8191] = -np.inf
+    a[11::12289] = -1.5
+    a[-1] = 39.99999
+    t = torch.from_numpy(a).cuda()
+    acc = torch.zeros(6, dtype=torch.float64, device="cuda")
+    hist = torch.zeros(40, dtype=torch.float64, device="cuda")
+    thr = (10.0, 20.0, 30.0)
+    for _ in range(2):
+        fs.fstat_stats(t, acc, thr, hist, 1.0)
+    torch.cuda.synchronize()
+    fin = a[np.isfinite(a)].astype(np.float64)
+    got = acc.cpu().numpy() / 2
+    assert got[0] == fin.size
+    assert abs(got[1] - fin.sum()) <= 1e-6 * abs(fin.sum())
+    assert abs(got[2] - (fin * fin).sum()) <= 1e-6 * (fin * fin).sum()
+    for i, th in enumerate(thr):
+        assert got[3 + i] == np.count_nonzero(fin > th)
+    x = fin[fin >= 0].astype(np.float32)
+    b = np.floor(x / np.float32(1.0)).astype(np.int64)
+    want = np.bincount(b[b < 40], minlength=40)
+    assert np.array_equal(hist.cpu().numpy() / 2, want)
+    # bins of width 2.5 (the quotient in FP32, as documented)
+    hist5 = torch.zeros(16, dtype=torch.float64, device="cuda")
+    acc1 = torch.zeros(3, dtype=torch.float64, device="cuda")
+    fs.fstat_stats(t, acc1, (), hist5, 2.5)
+    b5 = np.floor(x / np.float32(2.5)).astype(np.int64)
+    assert np.array_equal(hist5.cpu().numpy(), np.bincount(b5[b5 < 16], minlength=16))
+    assert acc1.cpu().numpy()[0] == fin.size
