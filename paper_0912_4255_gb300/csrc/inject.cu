@@ -5,13 +5,13 @@
 // tau = n dt + t_m(t_n), so that P is the signal phase with the heterodyne
 // f_h (t_n - t_start) removed (Sec. III.A.1).
 //
-// One block per knot interval of 1024 samples of one injection.  Two threads
-// evaluate the phase and the beam patterns with their derivatives in FP64 at
-// the interval's ends (the same Roemer delay and beam-pattern functions as
-// the time map); one thread turns them into cubic Hermite coefficients and
-// the phase factors exp(2 pi i P) at the start of each run of 256 samples
-// (from FP64 phases); every thread then evaluates its four samples in FP32
-// and rotates the run's factor by the phase offset of its sample.  Within a
+// Knot intervals of 1024 samples: the phase and the beam patterns with their
+// derivatives are evaluated in FP64 at the interval ends (the same Roemer
+// delay and beam-pattern functions as the time map) and turned into cubic
+// Hermite coefficients and the phase factors exp(2 pi i P) at the start of
+// each run of 256 samples (from FP64 phases); every thread then evaluates
+// its sample of each run in FP32 and rotates the run's factor by the phase
+// offset of its sample.  Within a
 // run the offset of sample v is c1 v + O(c2, c3): c1 is split as
 // c1_hi + c1_lo with c1_hi holding 16 significant bits, so c1_hi v (v < 256)
 // is exact in FP32 and its fractional part is taken exactly before the small
@@ -72,15 +72,24 @@ __device__ int check_injection(const PlanConst& pc, const fstat_injection& in, i
   return FSTAT_OK;
 }
 
-// grid (ceil(max_span / 1024), min(n_inj, 65535)); blocks stride over the
-// injections in y.
+// One block per segment of up to kInjSeg knot intervals of one injection
+// (grid (ceil(max_span / (kInjSeg H)), min(n_inj, 65535)); blocks stride over
+// the injections in y).  The FP64 work is spread over the lanes: one thread
+// per knot (phase, beams and their derivatives), one per interval (Hermite
+// coefficients), one per run (the phase factor at the run's start), since a
+// warp's FP64 instruction costs the same for one active lane as for 32.
+// Every thread then evaluates, interval by interval, one sample of each run
+// in FP32.
+constexpr int kInjSeg = 64;
+
 __global__ void __launch_bounds__(kInjThreads)
 k_inject(PlanConst pc, const fstat_injection* __restrict__ inj, int64_t n_inj, int64_t max_span,
          float2* __restrict__ x, int* status) {
-  __shared__ InjKnot kn[2];
-  __shared__ float cf[4];              // c1_hi, c1_lo, c2, c3
-  __shared__ float2 rot[kInjRuns];     // exp(2 pi i P) at the start of each run
-  __shared__ float ab[8];              // a0..a3, b0..b3
+  __shared__ InjKnot kn[kInjSeg + 1];
+  __shared__ double pcoef[kInjSeg][4];  // P0 (reduced), c1, c2, c3 of the phase
+  __shared__ float cf[kInjSeg][4];      // c1_hi, c1_lo, c2, c3
+  __shared__ float ab[kInjSeg][8];      // a0..a3, b0..b3
+  __shared__ float2 rot[kInjSeg][kInjRuns];   // exp(2 pi i P) at the start of each run
   for (int64_t j = blockIdx.y; j < n_inj; j += gridDim.y) {
     const fstat_injection in = inj[j];
     const int st = check_injection(pc, in, max_span);
@@ -88,34 +97,43 @@ k_inject(PlanConst pc, const fstat_injection* __restrict__ inj, int64_t n_inj, i
       if (blockIdx.x == 0 && threadIdx.x == 0) set_status(status, st);
       continue;
     }
-    const int64_t s0 = (int64_t)blockIdx.x << kInjLog2H;
+    const int64_t s0 = (int64_t)blockIdx.x * kInjSeg * kInjH;     // first sample of the segment
     if (s0 >= in.span_len) continue;
     const int64_t n0 = in.span_start + s0;
-    if (threadIdx.x < 2) {
+    const int64_t left = in.span_len - s0;
+    const int n_int = (int)(left >= (int64_t)kInjSeg * kInjH ? kInjSeg : (left + kInjH - 1) >> kInjLog2H);
+    // knots at the ends of the segment's intervals
+    if ((int)threadIdx.x <= n_int) {
       const Sky<double> sky = make_sky<double>(pc, in.alpha, in.delta);
       kn[threadIdx.x] = inj_knot(pc, sky, in, n0 + (int64_t)threadIdx.x * kInjH);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    // Hermite pieces of each interval
+    if ((int)threadIdx.x < n_int) {
+      const int i = threadIdx.x;
       double c1, c2, c3;
-      hermite3(kn[0].P, kn[0].dP, kn[1].P, kn[1].dP, &c1, &c2, &c3);
-      const double P0 = kn[0].P - floor(kn[0].P);
-      for (int r = 0; r < kInjRuns; ++r) {
-        const double u = (double)(r * kInjThreads);
-        const double base = P0 + u * (c1 + u * (c2 + u * c3));
-        double sb, cb;
-        sincospi(2.0 * (base - floor(base)), &sb, &cb);
-        rot[r] = make_float2((float)cb, (float)sb);
-      }
+      hermite3(kn[i].P, kn[i].dP, kn[i + 1].P, kn[i + 1].dP, &c1, &c2, &c3);
+      pcoef[i][0] = kn[i].P - floor(kn[i].P);
+      pcoef[i][1] = c1; pcoef[i][2] = c2; pcoef[i][3] = c3;
       const float hi = __int_as_float(__float_as_int((float)c1) & ~0xff);
-      cf[0] = hi;
-      cf[1] = (float)(c1 - (double)hi);
-      cf[2] = (float)c2;
-      cf[3] = (float)c3;
-      hermite3(kn[0].a, kn[0].da, kn[1].a, kn[1].da, &c1, &c2, &c3);
-      ab[0] = (float)kn[0].a; ab[1] = (float)c1; ab[2] = (float)c2; ab[3] = (float)c3;
-      hermite3(kn[0].b, kn[0].db, kn[1].b, kn[1].db, &c1, &c2, &c3);
-      ab[4] = (float)kn[0].b; ab[5] = (float)c1; ab[6] = (float)c2; ab[7] = (float)c3;
+      cf[i][0] = hi;
+      cf[i][1] = (float)(c1 - (double)hi);
+      cf[i][2] = (float)c2;
+      cf[i][3] = (float)c3;
+      hermite3(kn[i].a, kn[i].da, kn[i + 1].a, kn[i + 1].da, &c1, &c2, &c3);
+      ab[i][0] = (float)kn[i].a; ab[i][1] = (float)c1; ab[i][2] = (float)c2; ab[i][3] = (float)c3;
+      hermite3(kn[i].b, kn[i].db, kn[i + 1].b, kn[i + 1].db, &c1, &c2, &c3);
+      ab[i][4] = (float)kn[i].b; ab[i][5] = (float)c1; ab[i][6] = (float)c2; ab[i][7] = (float)c3;
+    }
+    __syncthreads();
+    // the phase factor at the start of each run, from the FP64 phase
+    for (int e = threadIdx.x; e < n_int * kInjRuns; e += kInjThreads) {
+      const int i = e / kInjRuns, r = e - i * kInjRuns;
+      const double u = (double)(r * kInjThreads);
+      const double base = pcoef[i][0] + u * (pcoef[i][1] + u * (pcoef[i][2] + u * pcoef[i][3]));
+      double sb, cb;
+      sincospi(2.0 * (base - floor(base)), &sb, &cb);
+      rot[i][r] = make_float2((float)cb, (float)sb);
     }
     __syncthreads();
     float s2p, c2p;
@@ -125,29 +143,32 @@ k_inject(PlanConst pc, const fstat_injection* __restrict__ inj, int64_t n_inj, i
     const float Ax = 0.5f * h0 * cosi;                          // 1/2 A_x
     const int v = threadIdx.x;
     const float fv = (float)v;
-    const float pv = cf[0] * fv;                 // exact
-    const float pv_frac = pv - floorf(pv);       // exact
-    const int64_t left = in.span_len - s0;
+#pragma unroll 1
+    for (int i = 0; i < n_int; ++i) {
+      const float pv = cf[i][0] * fv;              // exact
+      const float pv_frac = pv - floorf(pv);       // exact
+      const int64_t li = left - (int64_t)i * kInjH;
 #pragma unroll
-    for (int r = 0; r < kInjRuns; ++r) {
-      const int s = r * kInjThreads + v;
-      if (s >= left) break;
-      const float u = (float)(r * kInjThreads);
-      // (u + v)^2 - u^2 = v (2u + v); (u + v)^3 - u^3 = v (3u^2 + 3uv + v^2)
-      const float ph = pv_frac + cf[1] * fv + cf[2] * (fv * (2.0f * u + fv)) +
-                       cf[3] * (fv * (3.0f * u * u + 3.0f * u * fv + fv * fv));
-      float so, co;
-      sincospif(2.0f * ph, &so, &co);
-      const float2 b0 = rot[r];
-      const float cs = b0.x * co - b0.y * so, sn = b0.y * co + b0.x * so;
-      const float fs_ = (float)s;
-      const float a = ab[0] + fs_ * (ab[1] + fs_ * (ab[2] + fs_ * ab[3]));
-      const float b = ab[4] + fs_ * (ab[5] + fs_ * (ab[6] + fs_ * ab[7]));
-      const float Fp = a * c2p + b * s2p, Fx = b * c2p - a * s2p;
-      const float2 add = make_float2(Fp * Ap * cs + Fx * Ax * sn, Fp * Ap * sn - Fx * Ax * cs);
-      atomicAdd(x + n0 + s, add);
+      for (int r = 0; r < kInjRuns; ++r) {
+        const int s = r * kInjThreads + v;
+        if (s >= li) break;
+        const float u = (float)(r * kInjThreads);
+        // (u + v)^2 - u^2 = v (2u + v); (u + v)^3 - u^3 = v (3u^2 + 3uv + v^2)
+        const float ph = pv_frac + cf[i][1] * fv + cf[i][2] * (fv * (2.0f * u + fv)) +
+                         cf[i][3] * (fv * (3.0f * u * u + 3.0f * u * fv + fv * fv));
+        float so, co;
+        sincospif(2.0f * ph, &so, &co);
+        const float2 b0 = rot[i][r];
+        const float cs = b0.x * co - b0.y * so, sn = b0.y * co + b0.x * so;
+        const float fs_ = (float)s;
+        const float a = ab[i][0] + fs_ * (ab[i][1] + fs_ * (ab[i][2] + fs_ * ab[i][3]));
+        const float b = ab[i][4] + fs_ * (ab[i][5] + fs_ * (ab[i][6] + fs_ * ab[i][7]));
+        const float Fp = a * c2p + b * s2p, Fx = b * c2p - a * s2p;
+        const float2 add = make_float2(Fp * Ap * cs + Fx * Ax * sn, Fp * Ap * sn - Fx * Ax * cs);
+        atomicAdd(x + n0 + (int64_t)i * kInjH + s, add);
+      }
     }
-    __syncthreads();     // kn, cf, rot, ab are rewritten for the next injection
+    __syncthreads();     // kn, pcoef, cf, ab, rot are rewritten for the next injection
   }
 }
 
@@ -155,7 +176,7 @@ k_inject(PlanConst pc, const fstat_injection* __restrict__ inj, int64_t n_inj, i
 
 cudaError_t launch_inject(const PlanConst& pc, const fstat_injection* inj, int64_t n_inj, int64_t max_span,
                           float2* x, int* status, cudaStream_t s) {
-  const int64_t bx = (max_span + kInjH - 1) >> kInjLog2H;
+  const int64_t bx = (max_span + (int64_t)kInjSeg * kInjH - 1) / ((int64_t)kInjSeg * kInjH);
   if (n_inj <= 0 || bx <= 0) return cudaSuccess;
   if (bx > 0x7fffffff) return cudaErrorInvalidValue;
   const dim3 grid((unsigned)bx, (unsigned)(n_inj < 65535 ? n_inj : 65535));
