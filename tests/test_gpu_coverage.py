@@ -152,6 +152,51 @@ def test_ragged_batch_at_full_spans():
             assert r15(row[q], ref) <= TOL, i
 
 
+def test_persistent_launch_at_full_spans():
+    """The same ragged workload (1-10 d spans, FFT 2^18 .. 2^21 per
+    template, own gap lists) in one persistent launch replayed from a CUDA
+    graph, the batching design of the plan's persistent mode: every bin of
+    the 1-day template, sampled bins of the others."""
+    import torch
+    import paper_0912_4255_gb300 as fs
+    desc = synth.batch_plan(max_templates=6)
+    days = [1.0, 5.0, 10.0, 2.5, 7.3, 10.0]
+    tm, gaps = _span_templates(desc, days, synth.SEED_BASE + 36)
+    probe = fs.Plan(desc)
+    nb = fs.fstat_template_nb(probe, tm)
+    probe.close()
+    nf = np.array([max(synth.next_pow2(int(v)), 1 << 12) for v in nb], np.int64)
+    assert nf.min() == 1 << 18 and nf.max() == 1 << 21
+    tm["n_fft"] = nf
+    tm["out_off"] = np.concatenate([[0], np.cumsum(nf)[:-1]])
+    inj = synth.random_injection(synth.SEED_BASE + 37, df=0.07, fdot=-5e-10)
+    x, _ = injected_series(desc, synth.SEED_BASE + 38, [inj])
+    dev = torch.device("cuda:0")
+    plan = fs.Plan(desc.replace(n_fft=int(nf.max())), device=dev)
+    plan.set_tuning(mode=fs.MODE_PERSISTENT)
+    out = torch.full((int(nf.sum()),), float("nan"), device=dev)
+    runner = fs.GraphRunner(plan, torch.from_numpy(x).to(dev), fs.pack_templates(tm, device=dev),
+                            torch.from_numpy(gaps.reshape(-1).copy()).to(dev), out)
+    runner.replay()
+    runner.stream.synchronize()
+    assert fs.fstat_status(plan, runner.stream, raise_error=False) == 0
+    got = out.cpu().numpy()
+    plan.close()
+    xc = x.astype(np.complex128)
+    rng = synth.rng(9)
+    for i in range(len(tm)):
+        o, n = int(tm["out_off"][i]), int(nf[i])
+        g = gaps[int(tm["gap_off"][i]):int(tm["gap_off"][i]) + int(tm["n_gaps"][i])]
+        row = got[o:o + n]
+        assert np.all(np.isfinite(row)), i
+        if i == 0:
+            assert r15(row, F.resample_two_f(xc, tm[i], g, desc, n_fft=n)) <= TOL
+        else:
+            q = rng.integers(0, n, 12)
+            fr = (q - n // 2) / (n * desc.dt)
+            assert r15(row[q], F.single_bin_two_f_many(xc, tm[i], g, desc, fr)) <= TOL, i
+
+
 @pytest.mark.parametrize("mode", ["split", "fused", "plain"])
 def test_degenerate_template_inside_a_gap(mode):
     """A template whose whole span lies inside a gap has no valid sample:
