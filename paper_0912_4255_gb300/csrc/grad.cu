@@ -80,16 +80,18 @@ __device__ __forceinline__ bool last_block(int* counter, int nblocks) {
 
 // sinc(y) and its derivative; series near y = 0 avoids the cancellation of
 // (cos(pi y) - sinc(y)) / y
+// ry = 1 / y (used only when |y| >= 0.05): one reciprocal per tap serves
+// the sinc and, scaled, the window, instead of a division for each term.
 template <typename R>
-__device__ __forceinline__ void sinc_d(R y, R sy, R cy, R& s, R& ds) {
+__device__ __forceinline__ void sinc_d(R y, R ry, R sy, R cy, R& s, R& ds) {
   const R pi = (R)3.14159265358979323846;
   if (fabs(y) < (R)0.05) {
     const R p2 = pi * pi * y * y;
-    s = (R)1 - p2 / 6 + p2 * p2 / 120;
-    ds = pi * pi * y * ((R)(-1.0 / 3.0) + p2 / 30);
+    s = (R)1 - p2 * (R)(1.0 / 6) + p2 * p2 * (R)(1.0 / 120);
+    ds = pi * pi * y * ((R)(-1.0 / 3.0) + p2 * (R)(1.0 / 30));
   } else {
-    s = sy / (pi * y);
-    ds = (cy - s) / y;
+    s = sy * ry * (R)(1.0 / 3.14159265358979323846);
+    ds = (cy - s) * ry;
   }
 }
 
@@ -125,6 +127,7 @@ __device__ __forceinline__ bool sample_with_derivative(
   }
   const int taps = TAPS > 0 ? TAPS : pc.taps;
   const int half = taps >> 1;
+  const R ihalf = (R)1 / (R)half;
   const int jnn_off = (int)floor(dev + (R)0.5);
   const int jnn = ibase + jnn_off;
   const R dn = dev - (R)jnn_off;                // u - jnn in [-1/2, 1/2]
@@ -134,10 +137,10 @@ __device__ __forceinline__ bool sample_with_derivative(
   R S, Cd, sh, chh;
   if constexpr (std::is_same<R, float>::value) {
     sincospif(dn, &S, &Cd);
-    sincospif(dn / (R)half, &sh, &chh);
+    sincospif(dn * ihalf, &sh, &chh);
   } else {
     sincospi(dn, &S, &Cd);
-    sincospi(dn / (R)half, &sh, &chh);
+    sincospi(dn * ihalf, &sh, &chh);
   }
   const bool lanczos = pc.window == FSTAT_WIN_LANCZOS;
   C acc = czero<C>(), dacc = czero<C>();
@@ -150,15 +153,16 @@ __device__ __forceinline__ bool sample_with_derivative(
     const R xx = dn + (R)mq;
     const R sg = (mq & 1) ? (R)-1 : (R)1;
     R k0, k1;
-    sinc_d<R>(xx, sg * S, sg * Cd, k0, k1);
+    const R rx = (R)1 / xx;
+    sinc_d<R>(xx, rx, sg * S, sg * Cd, k0, k1);
     if (lanczos) {
       const R* wt = win_table<R>(wcs);
       const R cm = __ldg(wt + 2 * (mq + half)), sm = __ldg(wt + 2 * (mq + half) + 1);
       const R shm = sh * cm + chh * sm, chm = chh * cm - sh * sm;
       R w0, w1;
-      sinc_d<R>(xx / (R)half, shm, chm, w0, w1);
+      sinc_d<R>(xx * ihalf, rx * (R)half, shm, chm, w0, w1);
       const R kk = k0 * w0;
-      k1 = k1 * w0 + k0 * w1 / (R)half;
+      k1 = k1 * w0 + k0 * w1 * ihalf;
       k0 = kk;
     }
     const bool ok = gc.valid(j);
@@ -174,6 +178,21 @@ __device__ __forceinline__ bool sample_with_derivative(
   z = acc;
   dz = dacc;
   return msk;
+}
+
+// frac(s k) for the sample index k >= 0 without FP64 work per sample: with
+// F = frac(s) as a 64-bit binary fraction, F k mod 2^64 is exact in integer
+// arithmetic, and its top 24 bits are frac(s k) to FP32 precision (F itself
+// carries the 2^-53 rounding of the FP64 s, as the FP64 product s k would).
+// A warp's FP64 instruction costs 64 issue cycles at this GPU's FP64 rate,
+// so the four FP64 operations of frac(s k) per sample were the kernels'
+// largest cost.
+__device__ __forceinline__ unsigned long long frac_fix64(double s) {
+  const double f = s - floor(s);                  // [0, 1)
+  return __double2ull_rz(f * 18446744073709551616.0);   // f 2^64 < 2^64
+}
+__device__ __forceinline__ float frac_mul(unsigned long long F, int k) {
+  return (float)((F * (unsigned long long)k) >> 40) * (1.0f / 16777216.0f);
 }
 
 template <typename R>
@@ -203,6 +222,7 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_fwd(GradArgs<R> g) {
   const double c0 = df * (m.tb0 - g.pc.t_start);
   const R c0f = (R)(c0 - floor(c0));
   const double fdt = df * g.pc.dt;
+  const unsigned long long fdt64 = frac_fix64(fdt);
   R far = 0, fai = 0, fbr = 0, fbi = 0, sa = 0, sb = 0, sc = 0;
   GapCursor gc = make_cursor(m, g.gaps);
   for (int k = blockIdx.x * kGradThreads + threadIdx.x; k < (int)m.n_b; k += kGradBlocks * kGradThreads) {
@@ -210,8 +230,14 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_fwd(GradArgs<R> g) {
     R aa, bb;
     if (!sample_weights<R, FSTAT_SINC, TAPS>(g.pc, kn, k, g.x, gc, g.wcs, wa, wb, aa, bb))
       continue;
-    const double ck = fdt * (double)k;
-    const C e = expm<R>((R)(ck - floor(ck)) + c0f);
+    R ckf;
+    if constexpr (std::is_same<R, float>::value) {
+      ckf = frac_mul(fdt64, k);
+    } else {
+      const double ck = fdt * (double)k;
+      ckf = (R)(ck - floor(ck));
+    }
+    const C e = expm<R>(ckf + c0f);
     const C xa = cmul(wa, e), xb = cmul(wb, e);
     far += xa.x; fai += xa.y; fbr += xb.x; fbi += xb.y;
     sa += aa * aa; sb += bb * bb; sc += aa * bb;
@@ -314,9 +340,10 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_adj(GradArgs<R> g) {
   const double c0 = df * (m.tb0 - pc.t_start);
   const R c0f = (R)(c0 - floor(c0));
   const double fdt = df * pc.dt;
+  const unsigned long long fdt64 = frac_fix64(fdt);
   const R Gar = (R)cot[0], Gai = (R)cot[1], Gbr = (R)cot[2], Gbi = (R)cot[3];
   const R gA = (R)cot[4], gB = (R)cot[5], gC = (R)cot[6];
-  const R dtr = (R)pc.dt, fh = (R)pc.f_het, fdot = (R)tp.fdot, fddot = (R)tp.fddot;
+  const R dtr = (R)pc.dt, idtr = (R)(1.0 / pc.dt), fh = (R)pc.f_het, fdot = (R)tp.fdot, fddot = (R)tp.fddot;
   const R tb0r = (R)(m.tb0 - pc.t_start);
   const R rg0a = (R)g0a, rg0d = (R)g0d;
   const R rox = (R)ox, roy = (R)oy, roxa = (R)oxa, roya = (R)oya, roxd = (R)oxd, royd = (R)oyd;
@@ -352,8 +379,14 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_adj(GradArgs<R> g) {
     const R da_d = dad_T - rws * dadx * dTd, db_d = dbd_T - rws * dbdx * dTd;
     // phase Phi (cycles) and its derivatives
     const R taub = tb0r + (R)k * dtr;
-    const double ck = fdt * (double)k;
-    const R cyc = ph + (R)(ck - floor(ck)) + c0f;
+    R ckf;
+    if constexpr (std::is_same<R, float>::value) {
+      ckf = frac_mul(fdt64, k);
+    } else {
+      const double ck = fdt * (double)k;
+      ckf = (R)(ck - floor(ck));
+    }
+    const R cyc = ph + ckf + c0f;
     const C e = expm<R>(cyc);
     const R fb = taub * (fdot + (R)0.5 * fddot * taub) + (R)df;   // d(Phi_s + df tau_b)/dt_b, cycles/s
     const R dPa = fh * (rg0a - dTa) + fb * rg0a;
@@ -362,7 +395,7 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_adj(GradArgs<R> g) {
     const C y = cmul(z, e);
     const C dy = cmul(dz, e);
     // dW_a/dtheta = da y + a (dy du/dtheta - 2 pi i y dPhi)
-    const R dua = dTa / dtr, dud = dTd / dtr;
+    const R dua = dTa * idtr, dud = dTd * idtr;
     // helper: Re(conj(G) * V) = Gr Vr + Gi Vi
     auto contrib = [&](R dA, R dB, R du, R dP) {
       // V_a = dA y + a (du dy - 2 pi i dP y) ; -2 pi i dP y = 2 pi dP (y.y, -y.x)
