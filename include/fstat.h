@@ -366,7 +366,7 @@ int fstat_stats(const float *twoF, int64_t n, const float *thr, int n_thr, float
  * give one rounding per sample.  The detector response and phase are
  * evaluated in FP64 at knots every 1024 samples and joined by cubic Hermite
  * pieces, as in the time map.  Host errors: EINVAL (null or misaligned
- * pointer, n_inj < 0, max_span_len < 0), ERANGE (max_span_len above 2^41
+ * pointer, n_inj < 0, max_span_len < 0), ERANGE (max_span_len above 2^47
  * samples), ECUDA.  Asynchronous on stream. */
 int fstat_inject(fstat_plan_t p, const fstat_injection *injections, int64_t n_inj,
                  int64_t max_span_len, float *x_h, void *stream);
