@@ -31,6 +31,14 @@ def _log2(n: int) -> int:
     return int(n).bit_length() - 1
 
 
+def default_knot_log2(f_het: float, dt: float) -> int:
+    """The library's default knot spacing of the time map (log2 of grid
+    points per knot): 11 while |f_het dt| <= 50 and dt <= 0.5 s, 10 up to
+    100, 9 beyond; the autotuner tries the next denser spacing."""
+    c = abs(f_het * dt)
+    return 11 if (c <= 50.0 and dt <= 0.5) else (10 if c <= 100.0 else 9)
+
+
 def candidates(desc, modes=None, chunks=None, knots=True):
     """Tunings worth timing for a plan: every valid first-pass length
     (2^6 <= N1, N2 <= 2^12) in split mode, the default shape in the other
@@ -53,8 +61,7 @@ def candidates(desc, modes=None, chunks=None, knots=True):
         for c in chunks:
             out.append(dict(mode=MODE_SPLIT, chunk=int(c)))
     if knots:
-        default_h = 10 if abs(desc.f_het * desc.dt) <= 100.0 else 9
-        out.append(dict(mode=MODE_SPLIT, knot_log2=default_h - 1))
+        out.append(dict(mode=MODE_SPLIT, knot_log2=default_knot_log2(desc.f_het, desc.dt) - 1))
     return out
 
 

@@ -74,8 +74,7 @@ int choose_shape(fstat_plan_s* p) {
   p->sh.rows = rows_per_block(p->d.precision, l2);
   if (p->sh.cols <= 0 || p->sh.rows <= 0 || p->sh.cols > (1 << l2) || p->sh.rows > (1 << l1))
     return FSTAT_ENOTSUP;
-  p->pc.log2h = p->tune.knot_log2 ? p->tune.knot_log2
-              : (fabs(p->d.f_het * p->d.dt) <= 100.0 ? 10 : 9);
+  p->pc.log2h = p->tune.knot_log2 ? p->tune.knot_log2 : default_knot_log2(p->d.f_het, p->d.dt);
   if (p->pc.log2h < 4 || p->pc.log2h > 14) return FSTAT_ERANGE;
   const int64_t n = (int64_t)1 << L;
   const int64_t zbytes = 2 * n * p->cplx_bytes;

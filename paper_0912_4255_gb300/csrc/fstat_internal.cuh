@@ -993,6 +993,18 @@ struct Shape {
 // Default factorisation N = N1 N2 of the four-step FFT: the longest first
 // pass (N1 <= 2^12, N2 >= 2^6), so that a second-pass block holds as many
 // rows as its shared memory allows and its 2F stores form longer runs.
+// Knot spacing of the time map, 2^log2h grid points.  The cubic Hermite
+// pieces between knots err by about (w h)^4 / 384 relative, w the fastest
+// angular rate in the time delay and the beam patterns (twice the sidereal
+// rate, for a and b): 1.3e-6 at h dt = 1024 s.  The phase within a piece
+// is evaluated in FP32, so its span in cycles bounds h too: 2^11 points
+// while |f_het dt| <= 50 cycles per sample and dt <= 0.5 s, 2^10 to 100,
+// 2^9 beyond.
+__host__ __device__ inline int default_knot_log2(double f_het, double dt) {
+  const double c = fabs(f_het * dt);
+  return (c <= 50.0 && dt <= 0.5) ? 11 : (c <= 100.0 ? 10 : 9);
+}
+
 __host__ __device__ inline int default_log2_n1(int L) {
   int l1 = L - 6;
   if (l1 > 12) l1 = 12;

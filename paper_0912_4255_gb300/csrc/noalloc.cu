@@ -192,7 +192,8 @@ extern "C" int fstat_compute_noalloc(const fstat_plan_desc* d, const float* x_h,
   pc.lat = d->det.lat_rad; pc.lon = d->det.lon_rad; pc.gamma = d->det.gamma_rad; pc.radius = d->det.radius_m;
   pc.au = d->eph.au_m; pc.year = d->eph.year_s; pc.sid = d->eph.sidereal_day_s;
   pc.obliq = d->eph.obliquity_rad; pc.orb0 = d->eph.orb_phase0; pc.sid0 = d->eph.sid_phase0;
-  pc.log2h = fabs(d->f_het * d->dt) <= 100.0 ? 10 : kNaMinLog2h;
+  pc.log2h = default_knot_log2(d->f_het, d->dt);
+  if (pc.log2h < kNaMinLog2h) pc.log2h = kNaMinLog2h;
   pc.pad_ = 0;
   derive_constants(pc);
   pc.band_lo = 0;

@@ -12,7 +12,7 @@ def test_candidates_cover_every_valid_factorisation():
     split_l1 = sorted(t["log2_n1"] for t in c if t.get("mode") == MODE_SPLIT and "log2_n1" in t)
     assert split_l1 == [10, 11, 12]                         # N1, N2 within 2^6 .. 2^12
     assert {t["mode"] for t in c} == {MODE_SPLIT, MODE_FUSED, MODE_PERSISTENT}
-    assert {"mode": MODE_SPLIT, "knot_log2": 9} in c        # denser knots only
+    assert {"mode": MODE_SPLIT, "knot_log2": 10} in c       # denser knots only (the default is 11 here)
     small = synth.PlanDesc(dt=0.5, n_data=60000, n_fft=1 << 17, max_templates=4)
     assert sorted(t["log2_n1"] for t in at.candidates(small) if t.get("mode") == MODE_SPLIT
                   and "log2_n1" in t) == [6, 7, 8, 9, 10, 11]

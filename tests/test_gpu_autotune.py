@@ -44,3 +44,17 @@ def test_autotune_picks_a_valid_shape(tmp_path):
     assert plan2.tuning()["mode"] == res["tuning"]["mode"]
     again = at.autotune(plan2, xd, td, gd, cache=cache)
     assert again["cached"]
+
+
+def test_default_knot_spacing_matches_the_host_rule():
+    """The plan's default knot spacing is the rule the autotuner mirrors:
+    2^11 points for the searches at 0.5 s and 100 Hz, 2^10 up to 100 cycles
+    per sample, 2^9 beyond, and 2^10 at dt = 1 s."""
+    import torch
+    import paper_0912_4255_gb300 as fs
+    from paper_0912_4255_gb300 import autotune as at
+    for f_het, dt, want in [(100.0, 0.5, 11), (150.0, 0.5, 10), (1000.0, 0.25, 9), (40.0, 1.0, 10)]:
+        d = synth.PlanDesc(dt=dt, n_data=50000, n_fft=1 << 17, f_het=f_het, max_templates=1)
+        plan = fs.Plan(d, device=torch.device("cuda:0"))
+        assert plan.tuning()["knot_log2"] == want == at.default_knot_log2(f_het, dt)
+        plan.close()
