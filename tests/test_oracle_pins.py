@@ -583,3 +583,33 @@ def test_span_inside_a_gap_has_no_statistic():
     assert r["A"] * r["B"] - r["C"] ** 2 > 0.0
     assert 0.4 < np.mean(r["m"]) < 0.6
     assert np.all(np.isfinite(F.resample_two_f(x, tm[1], gaps, desc)))
+
+
+def test_two_f_invariances():
+    """Eq. 6 is a quadratic form F^H M^-1 F with M = [[A, C], [C, B]]: it
+    is unchanged by a common phase of the data, by scaling the data and
+    sigma^2 together, and by an orthogonal mixing of (a, b) (which mixes
+    F_a, F_b and transforms A, B, C as M -> R M R^T).  A wrong sign of the
+    cross term, or A and B swapped in it, fails the last check."""
+    g = synth.rng(77)
+    Fa = g.normal(size=64) + 1j * g.normal(size=64)
+    Fb = g.normal(size=64) + 1j * g.normal(size=64)
+    A, B, C = 3.0, 2.0, 0.7
+    ref = F.two_f(Fa, Fb, A, B, C, 1.0)
+    ph = np.exp(1j * 0.83)
+    assert np.allclose(F.two_f(Fa * ph, Fb * ph, A, B, C, 1.0), ref, rtol=1e-13, atol=0)
+    assert np.allclose(F.two_f(3.0 * Fa, 3.0 * Fb, A, B, C, 9.0), ref, rtol=1e-13, atol=0)
+    th = 0.61
+    c, s = np.cos(th), np.sin(th)
+    rot = np.array([[c, s], [-s, c]])
+    M2 = rot @ np.array([[A, C], [C, B]]) @ rot.T
+    Fa2, Fb2 = c * Fa + s * Fb, -s * Fa + c * Fb
+    assert np.allclose(F.two_f(Fa2, Fb2, M2[0, 0], M2[1, 1], M2[0, 1], 1.0), ref, rtol=1e-12, atol=0)
+    # the same through the whole oracle: a sky template's 2F does not change
+    # when the data carry a common phase
+    d = synth.tiny_plan(n_data=4000, n_fft=1 << 13, interp=R.SINC, taps=8)
+    x = synth.complex_noise(d.n_data, d.sigma2, 78).astype(np.complex128)
+    tm = synth.make_templates([1.1], [0.4], [0.0], 0, d.n_data)
+    a = F.resample_two_f(x, tm[0], np.zeros((0, 2), np.int64), d)
+    b = F.resample_two_f(x * ph, tm[0], np.zeros((0, 2), np.int64), d)
+    assert np.allclose(a, b, rtol=1e-10, atol=1e-12)
