@@ -240,3 +240,26 @@ def test_sky_edges_poles_and_angle_wrap():
     for i in range(len(tm)):
         assert r15(got[i], oracle_two_f(d, x, tm[i])) <= TOL, i
     assert np.max(got[0]) > 100                  # the injection, found at the pole
+
+
+def test_search_size_common_phase_invariance():
+    """A property that holds at any size (Eq. 6 depends on F_a, F_b only
+    through |F_a|^2, |F_b|^2 and F_a F_b*): the search-sized workload (10 d,
+    FFT 2^22, gaps, 8-tap Lanczos), its data multiplied by a common phase,
+    gives the same 2F in every bin of four templates to FP32 rounding."""
+    import torch
+    import paper_0912_4255_gb300 as fs
+    d = synth.search_plan(max_templates=4)
+    gaps = synth.gap_intervals(d.n_data, 0.10, 7200, 43200, seed=synth.SEED_BASE + 1)
+    x, _ = injected_series(d, synth.SEED_BASE + 39, [synth.random_injection(synth.SEED_BASE + 40, df=0.2)], gaps)
+    a, dl = synth.random_sky(4, synth.SEED_BASE + 41)
+    tm = synth.make_templates(a, dl, np.linspace(-1e-9, 0.0, 4), 0, d.n_data, 0, len(gaps))
+    dev = torch.device("cuda:0")
+    plan = fs.Plan(d, device=dev)
+    ref, rc = run_compute(d, x, tm, gaps, plan=plan)
+    assert rc == 0
+    ph = np.complex64(np.exp(1j * 2.2))
+    got, rc = run_compute(d, (x * ph).astype(np.complex64), tm, gaps, plan=plan)
+    assert rc == 0
+    plan.close()
+    assert r15(got, ref) <= 2e-6
